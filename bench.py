@@ -1,0 +1,380 @@
+"""Benchmark: matrix-free Hubbard H·v + Lanczos step on the 4x4 t-t' cluster (GB300).
+
+Workload (float64): 4x4 periodic square lattice, nearest-neighbour t = 1 and
+next-nearest t' = -0.3, U = 8, half filling N_up = N_dn = 8, D = 12870^2 =
+165,636,900 basis states.  One step = one three-term Lanczos iteration through
+the C ABI (`lanczos_step`): H·v with Paradeisos-ranked hop tables, the
+alpha/beta reductions and the vector updates.  The float64 vectors (1.33 GB
+each) are larger than L2, so no flush is needed between steps.
+
+Printed (one JSON line on rank 0): Gstates/s of the whole step, the roofline of
+the dominant kernel (H·v: 16 algorithmic bytes per state, read x + write y),
+end-to-end throughput with host buffers, time to E0 at 1e-10 for plain float64
+and for mixed precision, and the CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # the benchmark workload
+    "hubbard4x4_half": {"workload": "hubbard_4x4_tp-0.3_U8_half_filling", "L": 16,
+                        "lattice": "4x4 periodic, t=1, t'=-0.3", "U": 8.0, "N_up": 8, "N_dn": 8, "D": 165636900},
+    # smaller sector of the same cluster, for profiler captures (0.5 GB per vector, still > L2)
+    "hubbard4x4_n6": {"workload": "hubbard_4x4_tp-0.3_U8_6up_6dn", "L": 16,
+                      "lattice": "4x4 periodic, t=1, t'=-0.3", "U": 8.0, "N_up": 6, "N_dn": 6, "D": 64128064},
+}
+COMMON = {"vector_dtype": "f64",
+          "step": "one three-term Lanczos iteration (H·v + alpha/beta reductions + vector updates)",
+          "l2": "inputs larger than L2 (>= 0.5 GB per vector), no flush", "parallelism": "replicas"}
+METRIC = "H·v Gstates/s (Lanczos step)"
+UNIT = "Gstates/s"
+HV_BYTES_PER_STATE = 16  # float64: read x once, write y once
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="hubbard4x4_half", choices=sorted(WORKLOADS))
+    p.add_argument("--no-solve", action="store_true", help="skip the time-to-E0 runs")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("pd_hv.cu", "pd_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1707_03974_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch of the H·v kernel from the committed ncu summary, if it matches this source."""
+    p = os.path.join(ROOT, "profiles", "hv_dram_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash() or d.get("kernel") != kernel_key:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1707_03974_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    import paper_1707_03974_gb300 as pd
+    import workloads as wl
+
+    dev = torch.device("cuda", local)
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    wk = WORKLOADS[args.workload]
+    h = pd.Handle(cl.L, cl.bonds, cl.t, wk["U"], wk["N_up"], wk["N_dn"])
+    D = h.D
+    stream = torch.cuda.current_stream()
+    # inputs: a normalised random start vector (plumbing, outside the timed region)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234 + rank)
+    V = [torch.empty(D, dtype=torch.float64, device=dev) for _ in range(3)]
+    V[0].uniform_(-1.0, 1.0, generator=g)
+    V[0] /= V[0].norm()
+    nsteps = args.warmup + args.steps
+    alpha = torch.zeros(nsteps + 1, dtype=torch.float64, device=dev)
+    beta = torch.zeros(nsteps + 1, dtype=torch.float64, device=dev)
+    scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device=dev)
+    pd.hubbard_apply(h, V[0], V[1])  # builds the per-spin tables (setup, untimed)
+    torch.cuda.synchronize()
+
+    launches = ctypes.c_uint32(0)
+    ev_hv = []
+
+    def step(j, timed):
+        iv, ip, iw = j % 3, (j - 1) % 3, (j + 1) % 3
+        vprev = V[ip] if j > 0 else None
+        bprev = beta[j - 1:j] if j > 0 else None
+        e0 = e1 = None
+        if timed:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev_hv.append((e0, e1))
+        pd.lanczos_step(h, V[iv], vprev, V[iw], bprev, alpha[j:j + 1], beta[j:j + 1], scratch, e0, e1,
+                        launches if timed else None)
+
+    for j in range(args.warmup):
+        step(j, False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.4)
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for j in range(args.warmup, nsteps):
+        step(j, True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    hv_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_hv)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ab = beta[:nsteps].cpu().numpy()
+    sane = bool((ab > 0).all())
+
+    # end to end through the public API with host buffers: every step copies its input vector
+    # from pinned host memory and reads alpha, beta back to the host
+    host_v = torch.empty(D, dtype=torch.float64, pin_memory=True)
+    host_v.copy_(V[nsteps % 3])
+    host_ab = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    for j in range(e2e_steps):
+        V[0].copy_(host_v, non_blocking=True)
+        pd.lanczos_step(h, V[0], None, V[1], None, alpha[0:1], beta[0:1], scratch)
+        host_ab[0:1].copy_(alpha[0:1], non_blocking=True)
+        host_ab[1:2].copy_(beta[0:1], non_blocking=True)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = t0e.elapsed_time(t1e) / e2e_steps
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(e2e_t.item())
+
+    solve = None
+    if not args.no_solve and rank == 0 and args.workload == "hubbard4x4_half":
+        solve = time_to_e0(pd, h, torch)
+    del V, host_v
+    h.close()
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs") if peaks else 6800.0
+    achieved = HV_BYTES_PER_STATE * D / (hv_ms * 1e-3) / 1e9
+    traffic = ncu_traffic("k_hv<2,double,true>")
+    out = {
+        "metric": METRIC, "value": round(world * D / (ms * 1e-3) / 1e9, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random start vector)",
+        "config": {**WORKLOADS[args.workload], **COMMON},
+        "hv_ms": round(hv_ms, 4), "hv_gstates_per_s": round(D / (hv_ms * 1e-3) / 1e9, 4),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "k_hv<2,double,true>", "bytes_per_state": HV_BYTES_PER_STATE,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
+        "e2e": {"value": round(world * D / (e2e_ms * 1e-3) / 1e9, 4), "unit": UNIT,
+                "h2d_bytes_per_step": D * 8, "d2h_bytes_per_step": 16},
+        "gpu_launches": int(launches.value),
+        "clocks": clk,
+        "recurrence_sane": sane,
+    }
+    if solve:
+        out["time_to_E0"] = solve
+    if not args.no_cpu and args.workload == "hubbard4x4_half":
+        out["cpu_baseline"] = cpu_baseline(sample_rows=20000)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def time_to_e0(pd, h, torch):
+    """Wall time to E0 at 1e-10: plain float64 Lanczos vs float32 vectors + float64 finish (same seed)."""
+    gold = None
+    try:
+        gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_energies.json")))["square4x4_tp-0.3_U8_8_8"]["E0"]
+    except Exception:
+        pass
+    res = {}
+    for name, kw in (("plain_f64", dict(dtype=torch.float64)),
+                     ("mixed_f32_f64finish", dict(dtype=torch.float32, fp64_finish=True))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0, raise_on_error=False, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"seconds": round(dt, 4), "iterations": r.iterations, "iterations_f32": r.iterations_f32,
+                     "E0": r.E0, "residual": r.residual, "converged": r.converged,
+                     "abs_err_vs_oracle": (abs(r.E0 - gold) if gold is not None else None)}
+    return res
+
+
+def cpu_baseline(sample_rows: int):
+    """The CPU oracle as it stands (sorted list + binary search, float64) on a bounded sample of rows."""
+    import numpy as np
+
+    import workloads as wl
+    from oracle.basis import Basis
+    from oracle.hamiltonian import Model, apply_rows
+    from oracle.lanczos import start_vector
+
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    m = Model.from_cluster(cl, 8.0, 8, 8)
+    b = Basis(16, 8, 8)
+    x = start_vector(0, b.D)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.integers(0, b.D, sample_rows))
+    t0 = time.perf_counter()
+    apply_rows(m, b, x, rows)
+    dt = time.perf_counter() - t0
+    return {"value": round(sample_rows / dt / 1e9, 9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"H·v rows by definition (binary search in the sorted 165,636,900-entry list) for "
+                      f"{sample_rows} random rows of the same workload; {dt:.2f} s"}
+
+
+# ------------------------------------------------------------------ reference arm: the CPU oracle
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import workloads as wl
+    from oracle.basis import Basis
+    from oracle.hamiltonian import Model, apply_rows
+    from oracle.lanczos import start_vector
+
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    m = Model.from_cluster(cl, 8.0, 8, 8)
+    b = Basis(16, 8, 8)
+    x = start_vector(0, b.D)
+    v_prev = start_vector(1, b.D)
+    rng = np.random.default_rng(0)
+    sample = 10000
+    times = []
+    for j in range(args.warmup + args.steps):
+        rows = np.sort(rng.integers(0, b.D, sample))
+        t0 = time.perf_counter()
+        w = apply_rows(m, b, x, rows)  # H·v on the sampled rows
+        w -= 0.5 * v_prev[rows]           # recurrence on the same rows
+        a = float(np.dot(w, x[rows]))
+        w -= a * x[rows]
+        float(np.linalg.norm(w))
+        dt = time.perf_counter() - t0
+        if j >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = sample / (ms * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": round(value, 9), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+           "config": {**WORKLOADS["hubbard4x4_half"], **COMMON},
+           "impl": "reference",
+           "cpu_baseline": {"value": round(value, 9), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{sample} random rows per step of the same workload, oracle H·v by "
+                                      f"binary search plus the recurrence on those rows"},
+           "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return out
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

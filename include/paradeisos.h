@@ -1,0 +1,202 @@
+/*
+ * paradeisos.h -- C ABI of the GB300 (sm_103a) library for matrix-free exact
+ * diagonalisation of the single-band Hubbard model with Paradeisos basis
+ * ranking (Jia, Wang, Mendl, Moritz, Devereaux, arXiv 1707.03974).
+ *
+ * Conventions used by every entry point (Sec. II A and Sec. III of the paper):
+ *   - site i of an L-site cluster is bit i of an occupation string;
+ *   - a combined basis state is the 64-bit integer (up << L) | dn, the
+ *     spin-down string in the L low bits;
+ *   - the per-spin position of a string with n particles is its index in the
+ *     ascending list of L-bit integers with n bits set (the "forward map",
+ *     Eq. 3); the combined index is I = C(L, N_dn) * idx_up + idx_dn;
+ *   - a vector over the basis is stored densely in combined-index order, i.e.
+ *     as a row-major D_up x D_dn matrix.
+ *
+ * Memory: every vector, state or index pointer passed in is caller-owned DEVICE
+ * memory on the handle's device (in the Python binding: torch tensors).  The
+ * library never frees caller memory.  A handle owns only its own small tables
+ * (binomial lookup table, per-spin strings and hop lists: O(sqrt D) entries),
+ * allocated on the current device at creation.  Calls that take a `stream`
+ * enqueue work on that CUDA stream (a cudaStream_t passed as void*, NULL = the
+ * legacy default stream) and return without synchronising unless stated.
+ * A handle may be used by one stream at a time.
+ *
+ * Errors: argument errors are returned synchronously.  Per-element problems
+ * detected on the device (a string with the wrong popcount, an index >= D)
+ * write the sentinel UINT64_MAX to that output element and set a sticky flag
+ * on the handle, read (and cleared) by hubbard_last_error().  Device code never
+ * traps or asserts.
+ */
+#ifndef PARADEISOS_H
+#define PARADEISOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hb_basis *hb_handle;
+
+typedef enum {
+    HB_OK = 0,
+    HB_ERR_INVALID_ARG = 1,   /* bad argument (range, duplicate bond, aliasing, null) */
+    HB_ERR_OVERFLOW = 2,      /* D would not fit the index type */
+    HB_ERR_INVALID_STATE = 3, /* rank: a string with the wrong popcount or bits >= L */
+    HB_ERR_OUT_OF_RANGE = 4,  /* unrank: an index >= D */
+    HB_ERR_NO_MEMORY = 5,     /* a table or the workspace does not fit */
+    HB_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    HB_ERR_NOT_CONVERGED = 7, /* Lanczos hit maxit; best estimate returned */
+    HB_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up */
+} hb_status;
+
+typedef enum {
+    HB_F64 = 0, /* IEEE binary64 vectors */
+    HB_F32 = 1  /* IEEE binary32 vectors */
+} hb_dtype;
+
+/* Human-readable name of a status code (static string). */
+const char *hb_status_string(hb_status s);
+
+/*
+ * Create the Hubbard problem of Eq. 1 on one cluster and one (N_up, N_dn) sector.
+ *   H = - sum_bonds t_b sum_sigma (c+_{i sigma} c_{j sigma} + h.c.) + U sum_i n_{i up} n_{i dn}
+ * L       number of sites, 1 <= L <= 32.
+ * bonds   host array [n_bonds][2] of site pairs (i, j), 0 <= i, j < L, i != j;
+ *         each unordered pair at most once (a duplicate is HB_ERR_INVALID_ARG).
+ *         Every bond contributes both hop directions.
+ * t       host array [n_bonds] of hopping amplitudes t_b (matrix element -t_b
+ *         times the fermion sign of Sec. II B).
+ * N_up, N_dn  particle numbers, 0 <= N <= L.  D = C(L,N_up) C(L,N_dn) must be < 2^63.
+ * out     receives the handle.  Tables are built on the current CUDA device,
+ *         synchronously.  The per-spin hop lists are built lazily on first use
+ *         of hubbard_apply / hubbard_row_entries / lanczos_ground_state.
+ */
+hb_status hubbard_basis_create(int L, int n_bonds, const int32_t *bonds, const double *t, double U,
+                               int N_up, int N_dn, hb_handle *out);
+hb_status hubbard_basis_destroy(hb_handle h);
+/* D, D_up = C(L,N_up), D_dn = C(L,N_dn); any pointer may be NULL. */
+hb_status hubbard_basis_dim(hb_handle h, uint64_t *D, uint64_t *D_up, uint64_t *D_dn);
+/* Change U (the interaction of Eq. 1) without rebuilding any table. */
+hb_status hubbard_set_U(hb_handle h, double U);
+
+/*
+ * Paradeisos forward map, batched (Eq. 3 and the combined index of Sec. III).
+ * states  device [n] combined strings (up << L) | dn
+ * idx     device [n] output combined indices; UINT64_MAX (and the sticky flag
+ *         HB_ERR_INVALID_STATE) for a string whose popcounts differ from
+ *         (N_up, N_dn) or that has bits at or above L in either half.
+ */
+hb_status paradeisos_rank(hb_handle h, const uint64_t *states, uint64_t *idx, uint64_t n, void *stream);
+
+/*
+ * Paradeisos backward map, batched (the backward-map procedure of Sec. III).
+ * idx     device [n] combined indices
+ * states  device [n] output strings (up << L) | dn; UINT64_MAX (and the sticky
+ *         flag HB_ERR_OUT_OF_RANGE) for an index >= D.
+ */
+hb_status paradeisos_unrank(hb_handle h, const uint64_t *idx, uint64_t *states, uint64_t n, void *stream);
+
+/*
+ * y = H x, matrix-free (Eq. 1): diagonal U * popcount(up & dn) (Sec. II B) plus
+ * every hop of both spins, each target located by the forward map.
+ * dt      HB_F64 or HB_F32: element type of x and y (length D each).
+ * x, y    device vectors; must not overlap (HB_ERR_INVALID_ARG).
+ */
+hb_status hubbard_apply(hb_handle h, hb_dtype dt, const void *x, void *y, void *stream);
+
+/*
+ * Verification export of matrix rows row0 .. row0+nrows-1 in canonical form:
+ * entries sorted by column, the diagonal included even when it is zero.
+ * cols, vals  device [nrows][max_entries]; counts device [nrows].
+ * A row with more than max_entries entries sets counts[r] = UINT32_MAX and
+ * the sticky flag HB_ERR_INVALID_ARG.  (1 + 2 * n_bonds always suffices.)
+ */
+hb_status hubbard_row_entries(hb_handle h, uint64_t row0, uint32_t nrows, uint32_t max_entries,
+                              uint64_t *cols, double *vals, uint32_t *counts, void *stream);
+
+/* Sticky device-side error of the handle: synchronises the device, returns
+ * HB_OK or the first per-element error recorded since the last call, and clears it. */
+hb_status hubbard_last_error(hb_handle h);
+
+/* ---------------- Lanczos ground state (the solver the paper cites in Sec. I) ---- */
+
+typedef struct {
+    int32_t maxit;        /* maximum Lanczos steps (>= 1) */
+    int32_t reorth;       /* 0: three-term recurrence; 1: full reorthogonalisation
+                             (classical Gram-Schmidt twice against all stored vectors) */
+    int32_t vec_dtype;    /* hb_dtype of the Krylov vectors */
+    int32_t check_every;  /* Ritz check every k steps (>= 1) */
+    double tol;           /* stop when beta_j |s_last| <= tol * max(1, |theta|); <= 0: run maxit */
+    uint64_t seed;        /* start vector when v0 == NULL: SplitMix64, element i = output i+1
+                             of the stream seeded with `seed`, mapped to [-1, 1), normalised */
+    int32_t fp64_finish;  /* with vec_dtype HB_F32: after the binary32 phase stalls, form the
+                             Ritz vector and continue in binary64 until tol is met */
+    int32_t f32_tol_exp;  /* binary32 phase ends when the residual <= 10^f32_tol_exp * max(1,|theta|)
+                             or stops improving (default -5 when 0) */
+} hb_lanczos_opts;
+
+typedef struct {
+    double E0;                 /* lowest Ritz value */
+    double residual;           /* beta_j |s_last| of the lowest Ritz pair */
+    int32_t iterations;        /* total Lanczos steps (all phases) */
+    int32_t iterations_f32;    /* steps taken in the binary32 phase */
+    int32_t status;            /* hb_status of the solve */
+    int32_t converged;         /* 1 if the tolerance was met */
+    double seconds;            /* host wall time of the call */
+} hb_lanczos_info;
+
+/* Bytes of device workspace lanczos_ground_state needs for these options. */
+hb_status lanczos_workspace_bytes(hb_handle h, const hb_lanczos_opts *opts, uint64_t *bytes);
+
+/*
+ * Lowest eigenvalue of H by Lanczos.  v0: device start vector of vec_dtype
+ * (length D, need not be normalised) or NULL for the seeded random start.
+ * workspace: caller-owned device buffer of at least lanczos_workspace_bytes.
+ * alphas, betas: optional HOST arrays [maxit] receiving the recurrence
+ * coefficients of the last phase (may be NULL).  Synchronises `stream`; returns
+ * HB_ERR_NOT_CONVERGED (with E0 filled) if maxit is reached first.
+ */
+hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *opts, const void *v0,
+                               void *workspace, uint64_t workspace_bytes,
+                               double *alphas, double *betas, double *E0, hb_lanczos_info *info,
+                               void *stream);
+
+/* Bytes of device scratch (per-block partial sums of the reductions) lanczos_step needs. */
+hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes);
+
+/*
+ * One step of the three-term Lanczos recurrence (the building block of
+ * lanczos_ground_state, exposed for drivers that keep their own loop):
+ *   w = H v - beta_prev * vprev;  alpha = <w, v>;  w -= alpha * v;  beta = ||w||;  w /= beta,
+ * after which w holds the next Lanczos vector.
+ * dt            element type of v, vprev, w (device vectors of length D; w must not
+ *               overlap v or vprev).
+ * vprev, beta_prev  previous vector and device scalar; both NULL on the first step.
+ * alpha, beta   device doubles written by the step (float64 reductions as in
+ *               lanczos_ground_state).
+ * scratch       caller-owned device buffer of lanczos_step_scratch_bytes bytes.
+ * ev_hv_begin, ev_hv_end  optional cudaEvent_t (as void*) recorded on `stream`
+ *               just before and just after the H·v kernel (a timing hook; NULL to skip).
+ * launches      optional host counter, incremented by the number of kernels enqueued (6).
+ * Asynchronous on `stream`.
+ */
+hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w, const double *beta_prev,
+                       double *alpha, double *beta, void *scratch, uint64_t scratch_bytes, void *ev_hv_begin,
+                       void *ev_hv_end, uint32_t *launches, void *stream);
+
+/*
+ * Host utility (no GPU needed): lowest eigenvalue theta of the symmetric
+ * tridiagonal matrix with diagonal alpha[0..n) and off-diagonal beta[0..n-1),
+ * by Sturm-sequence bisection, and the last component of its normalised
+ * eigenvector by inverse iteration (the Ritz residual of Lanczos step n-1 is
+ * beta[n-1] * |s_last|).  Used by lanczos_ground_state after every check.
+ */
+hb_status hb_tridiag_lowest(const double *alpha, const double *beta, int n, double *theta, double *s_last);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARADEISOS_H */

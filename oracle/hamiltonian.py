@@ -122,6 +122,26 @@ def apply(model: Model, basis: Basis, x: np.ndarray) -> np.ndarray:
     return y
 
 
+def apply_rows(model: Model, basis: Basis, x: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """(H x)[rows]: the same term-by-term evaluation as `apply`, restricted to some rows."""
+    L = model.L
+    rows = np.asarray(rows, dtype=np.int64)
+    states = basis.combined[rows]
+    up, dn = basis.split(states)
+    y = model.U * popcount64(up & dn).astype(np.float64) * x[rows]
+    for b in range(len(model.t)):
+        i, j = int(model.bonds[b, 0]), int(model.bonds[b, 1])
+        for spin in (0, 1):
+            s = up if spin == 0 else dn
+            valid, s2, sign = hop_targets(s, i, j)
+            target = (s2 << np.uint64(L)) | dn if spin == 0 else (up << np.uint64(L)) | s2
+            k = np.nonzero(valid)[0]
+            cols = basis.index_of(target[k])
+            assert np.all(cols >= 0)
+            y[k] += -model.t[b] * sign[k] * x[cols]
+    return y
+
+
 def dense(model: Model, basis: Basis) -> np.ndarray:
     """Dense H (small clusters only), assembled row by row from `row`."""
     if basis.D > 6000:
@@ -219,6 +239,14 @@ class KronOperator:
                                     *[P(k.ctypes.data) for k in keep], ctypes.c_double(self.model.U),
                                     P(x.ctypes.data), P(y.ctypes.data))
         return y
+
+    def abs_apply(self, x: np.ndarray) -> np.ndarray:
+        """|H| |x| (entrywise absolute values): the scale of the rounding error of every row sum."""
+        X = np.abs(np.asarray(x, dtype=np.float64)).reshape(self.D_up, self.D_dn)
+        Y = abs(self.model.U) * self.docc * X
+        Y += abs(self.A) @ X
+        Y += (abs(self.B) @ X.T).T
+        return Y.reshape(-1)
 
     def diag_row_sums(self):
         """Row sums of |H| (used for error bounds in tests)."""

@@ -1,0 +1,298 @@
+"""ctypes binding of libparadeisos.so: argument marshalling only.
+
+Every function here forwards to the C entry point of the same name declared in
+include/paradeisos.h.  Device buffers are torch CUDA tensors (torch provides
+memory and streams); all computation happens in the library's CUDA kernels.
+If the library has not been built, every call raises: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libparadeisos.so")
+
+HB_F64, HB_F32 = 0, 1
+STATUS = {0: "HB_OK", 1: "HB_ERR_INVALID_ARG", 2: "HB_ERR_OVERFLOW", 3: "HB_ERR_INVALID_STATE",
+          4: "HB_ERR_OUT_OF_RANGE", 5: "HB_ERR_NO_MEMORY", 6: "HB_ERR_CUDA", 7: "HB_ERR_NOT_CONVERGED",
+          8: "HB_ERR_TIMEOUT"}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
+
+_lib = None
+
+
+class HubbardError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        self.name = STATUS.get(status, f"HB_STATUS_{status}")
+        super().__init__(f"{where}: {self.name}")
+
+
+class LanczosOpts(ctypes.Structure):
+    _fields_ = [("maxit", ctypes.c_int32), ("reorth", ctypes.c_int32), ("vec_dtype", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("fp64_finish", ctypes.c_int32), ("f32_tol_exp", ctypes.c_int32)]
+
+
+class LanczosInfo(ctypes.Structure):
+    _fields_ = [("E0", ctypes.c_double), ("residual", ctypes.c_double), ("iterations", ctypes.c_int32),
+                ("iterations_f32", ctypes.c_int32), ("status", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("seconds", ctypes.c_double)]
+
+
+def load():
+    """Load libparadeisos.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libparadeisos.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, U64, I32, D = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "hb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "hubbard_basis_create": (ctypes.c_int, [I32, I32, P, P, D, I32, I32, ctypes.POINTER(P)]),
+        "hubbard_basis_destroy": (ctypes.c_int, [P]),
+        "hubbard_basis_dim": (ctypes.c_int, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]),
+        "hubbard_set_U": (ctypes.c_int, [P, D]),
+        "paradeisos_rank": (ctypes.c_int, [P, P, P, U64, P]),
+        "paradeisos_unrank": (ctypes.c_int, [P, P, P, U64, P]),
+        "hubbard_apply": (ctypes.c_int, [P, I32, P, P, P]),
+        "hubbard_row_entries": (ctypes.c_int, [P, U64, ctypes.c_uint32, ctypes.c_uint32, P, P, P, P]),
+        "hubbard_last_error": (ctypes.c_int, [P]),
+        "lanczos_workspace_bytes": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), ctypes.POINTER(U64)]),
+        "lanczos_ground_state": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, P, U64, P, P,
+                                                ctypes.POINTER(D), ctypes.POINTER(LanczosInfo), P]),
+        "hb_tridiag_lowest": (ctypes.c_int, [P, P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "lanczos_step_scratch_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
+        "lanczos_step": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, U64, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise HubbardError(status, where)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+# ---------------------------------------------------------------- handle + API
+
+class Handle:
+    """Owns one hb_handle (hubbard_basis_create / hubbard_basis_destroy)."""
+
+    def __init__(self, L: int, bonds: Sequence[Tuple[int, int]], t: Sequence[float], U: float, N_up: int, N_dn: int):
+        import numpy as np
+        lib = load()
+        b = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+        tt = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(-1))
+        if len(tt) != len(b):
+            raise ValueError("bonds and t differ in length")
+        h = ctypes.c_void_p()
+        _check(lib.hubbard_basis_create(int(L), len(b), ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(tt.ctypes.data),
+                                        float(U), int(N_up), int(N_dn), ctypes.byref(h)), "hubbard_basis_create")
+        self._h = h
+        self.L, self.N_up, self.N_dn, self.U = int(L), int(N_up), int(N_dn), float(U)
+        self.n_bonds = len(b)
+        D, Du, Dd = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib.hubbard_basis_dim(h, ctypes.byref(D), ctypes.byref(Du), ctypes.byref(Dd)), "hubbard_basis_dim")
+        self.D, self.D_up, self.D_dn = D.value, Du.value, Dd.value
+
+    @property
+    def ptr(self):
+        if self._h is None:
+            raise RuntimeError("handle destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().hubbard_basis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def hubbard_basis_create(L, bonds, t, U, N_up, N_dn) -> Handle:
+    return Handle(L, bonds, t, U, N_up, N_dn)
+
+
+def hubbard_basis_destroy(h: Handle):
+    h.close()
+
+
+def hubbard_set_U(h: Handle, U: float):
+    _check(load().hubbard_set_U(h.ptr, float(U)), "hubbard_set_U")
+    h.U = float(U)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("device (CUDA) tensor required")
+        if t is not None and not t.is_contiguous():
+            raise ValueError("contiguous tensor required")
+
+
+def paradeisos_rank(h: Handle, states, idx=None, stream=None):
+    """Combined indices of combined strings (uint64 bit patterns held in int64 tensors)."""
+    import torch
+    _need_cuda(states)
+    if idx is None:
+        idx = torch.empty_like(states)
+    _need_cuda(idx)
+    _check(load().paradeisos_rank(h.ptr, _ptr(states), _ptr(idx), states.numel(), _stream_ptr(stream)), "paradeisos_rank")
+    return idx
+
+
+def paradeisos_unrank(h: Handle, idx, states=None, stream=None):
+    import torch
+    _need_cuda(idx)
+    if states is None:
+        states = torch.empty_like(idx)
+    _need_cuda(states)
+    _check(load().paradeisos_unrank(h.ptr, _ptr(idx), _ptr(states), idx.numel(), _stream_ptr(stream)), "paradeisos_unrank")
+    return states
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return HB_F64
+    if t.dtype == torch.float32:
+        return HB_F32
+    raise ValueError("vectors must be float64 or float32")
+
+
+def hubbard_apply(h: Handle, x, y=None, stream=None):
+    """y = H x (matrix-free)."""
+    import torch
+    _need_cuda(x)
+    if x.numel() != h.D:
+        raise ValueError(f"x has {x.numel()} elements, D = {h.D}")
+    if y is None:
+        y = torch.empty_like(x)
+    _need_cuda(y)
+    if y.dtype != x.dtype or y.numel() != h.D:
+        raise ValueError("y must match x in dtype and size")
+    _check(load().hubbard_apply(h.ptr, _dtype_code(x), _ptr(x), _ptr(y), _stream_ptr(stream)), "hubbard_apply")
+    return y
+
+
+def hubbard_row_entries(h: Handle, row0: int, nrows: int, max_entries: Optional[int] = None, stream=None):
+    import torch
+    me = int(max_entries) if max_entries is not None else 1 + 2 * h.n_bonds
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cols = torch.empty((nrows, me), dtype=torch.int64, device=dev)
+    vals = torch.empty((nrows, me), dtype=torch.float64, device=dev)
+    counts = torch.empty((nrows,), dtype=torch.int32, device=dev)
+    _check(load().hubbard_row_entries(h.ptr, int(row0), int(nrows), me, _ptr(cols), _ptr(vals), _ptr(counts),
+                                      _stream_ptr(stream)), "hubbard_row_entries")
+    return cols, vals, counts
+
+
+def hubbard_last_error(h: Handle) -> str:
+    return STATUS[load().hubbard_last_error(h.ptr)]
+
+
+@dataclass
+class LanczosResult:
+    E0: float
+    residual: float
+    iterations: int
+    iterations_f32: int
+    status: str
+    converged: bool
+    seconds: float
+    alphas: list
+    betas: list
+
+
+def lanczos_ground_state(h: Handle, maxit: int = 300, tol: float = 1e-10, reorth: bool = False, dtype=None,
+                         seed: int = 0, v0=None, check_every: int = 1, fp64_finish: bool = False,
+                         f32_tol_exp: int = 0, workspace=None, stream=None, raise_on_error: bool = True) -> LanczosResult:
+    import torch
+    dt = HB_F64 if dtype in (None, torch.float64) else HB_F32
+    o = LanczosOpts(int(maxit), int(bool(reorth)), dt, int(check_every), float(tol), int(seed) & ((1 << 64) - 1),
+                    int(bool(fp64_finish)), int(f32_tol_exp))
+    lib = load()
+    nb = ctypes.c_uint64()
+    _check(lib.lanczos_workspace_bytes(h.ptr, ctypes.byref(o), ctypes.byref(nb)), "lanczos_workspace_bytes")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
+        workspace = torch.empty((max(1, nb.value),), dtype=torch.uint8, device=dev)
+    if v0 is not None:
+        _need_cuda(v0)
+        if _dtype_code(v0) != dt or v0.numel() != h.D:
+            raise ValueError("v0 must have the Krylov vector dtype and D elements")
+    import numpy as np
+    alphas = np.zeros(maxit + 1)
+    betas = np.zeros(maxit + 1)
+    E0 = ctypes.c_double(float("nan"))
+    info = LanczosInfo()
+    st = lib.lanczos_ground_state(h.ptr, ctypes.byref(o), _ptr(v0), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(),
+                                  ctypes.c_void_p(alphas.ctypes.data), ctypes.c_void_p(betas.ctypes.data),
+                                  ctypes.byref(E0), ctypes.byref(info), _stream_ptr(stream))
+    if st not in (0, 7) or (raise_on_error and st != 0):
+        raise HubbardError(st, "lanczos_ground_state")
+    n_last = info.iterations - info.iterations_f32 if (fp64_finish and info.iterations != info.iterations_f32) \
+        else info.iterations
+    return LanczosResult(E0.value, info.residual, info.iterations, info.iterations_f32, STATUS[st],
+                         bool(info.converged), info.seconds, alphas[:n_last].tolist(), betas[:n_last].tolist())
+
+
+def lanczos_step_scratch_bytes(h: Handle) -> int:
+    n = ctypes.c_uint64()
+    _check(load().lanczos_step_scratch_bytes(h.ptr, ctypes.byref(n)), "lanczos_step_scratch_bytes")
+    return n.value
+
+
+def lanczos_step(h: Handle, v, vprev, w, beta_prev, alpha, beta, scratch, ev_hv_begin=None, ev_hv_end=None,
+                 launches: Optional[ctypes.c_uint32] = None, stream=None):
+    """One three-term Lanczos step; alpha/beta/beta_prev are 1-element float64 CUDA tensors (or views)."""
+    _need_cuda(v, w)
+    code = _dtype_code(v)
+    ev0 = ctypes.c_void_p(ev_hv_begin.cuda_event) if ev_hv_begin is not None else ctypes.c_void_p(0)
+    ev1 = ctypes.c_void_p(ev_hv_end.cuda_event) if ev_hv_end is not None else ctypes.c_void_p(0)
+    _check(load().lanczos_step(h.ptr, code, _ptr(v), _ptr(vprev), _ptr(w), _ptr(beta_prev), _ptr(alpha), _ptr(beta),
+                               _ptr(scratch), scratch.numel() * scratch.element_size(), ev0, ev1,
+                               ctypes.byref(launches) if launches is not None else None, _stream_ptr(stream)),
+           "lanczos_step")
+
+
+def hb_tridiag_lowest(alpha, beta):
+    """Host utility of the library: lowest eigenvalue of a tridiagonal and its eigenvector's last entry."""
+    import numpy as np
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    th, sl = ctypes.c_double(), ctypes.c_double()
+    _check(load().hb_tridiag_lowest(ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(b.ctypes.data), len(a),
+                                    ctypes.byref(th), ctypes.byref(sl)), "hb_tridiag_lowest")
+    return th.value, sl.value

@@ -1,0 +1,152 @@
+"""GPU parity of the matrix-free H·v against the oracle.
+
+Tolerances: float64 vectors, normwise |y - y_ref|_inf <= 1e-12 |y_ref|_inf (the
+1e-12 relative bar) and, per element, <= 64 eps64 * sum_c |H_rc x_c| (the
+rounding bound of a sum of at most 1 + 2 n_bonds products).  float32 vectors:
+per element <= 64 eps32 * sum_c |H_rc x_c| against the float64 oracle applied to
+the same (float32-rounded) input.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle.basis import Basis
+from oracle.hamiltonian import KronOperator, Model, apply, row
+from oracle.lanczos import start_vector
+from tests.conftest import GOLDEN
+from tests.gpu_util import handle_for, need_gpu
+
+pytestmark = pytest.mark.gpu
+EPS64 = np.finfo(np.float64).eps
+EPS32 = np.finfo(np.float32).eps
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    return torch, pd
+
+
+def abs_bound(m, b, x):
+    """sum_c |H_rc x_c| for every row (the |H| |x| product), from the oracle."""
+    return KronOperator(m, use_c=False).abs_apply(x)
+
+
+CASES = [(wl.ring(8), 4, 4, 4.0), (wl.ring(8), 3, 5, 1.0), (wl.ring(6), 2, 3, 2.5), (wl.dimer(), 1, 1, 4.0),
+         (wl.rect_periodic(4, 3), 5, 3, 7.5), (wl.rect_periodic(3, 3, 1.0, -0.3), 4, 5, 8.0),
+         (wl.ring(12), 6, 6, 3.0), (wl.ring(10), 0, 5, 2.0), (wl.ring(10), 10, 3, 2.0), (wl.ring(7), 7, 7, 5.0)]
+
+
+@pytest.mark.parametrize("cl,nu,nd,U", CASES)
+def test_hv_f64_matches_oracle(env, cl, nu, nd, U):
+    torch, pd = env
+    m = Model.from_cluster(cl, U, nu, nd)
+    b = Basis(cl.L, nu, nd)
+    x = start_vector(7, b.D)
+    yr = apply(m, b, x)
+    h = handle_for(cl, U, nu, nd)
+    y = pd.hubbard_apply(h, torch.from_numpy(x).cuda()).cpu().numpy()
+    err = np.abs(y - yr)
+    assert err.max() <= 1e-12 * max(np.abs(yr).max(), 1e-300)
+    assert np.all(err <= 64 * EPS64 * abs_bound(m, b, x) + 1e-300)
+    h.close()
+
+
+@pytest.mark.parametrize("cl,nu,nd,U", CASES)
+def test_hv_f32_matches_oracle(env, cl, nu, nd, U):
+    torch, pd = env
+    m = Model.from_cluster(cl, U, nu, nd)
+    b = Basis(cl.L, nu, nd)
+    x32 = start_vector(8, b.D).astype(np.float32)
+    x = x32.astype(np.float64)
+    yr = apply(m, b, x)
+    h = handle_for(cl, U, nu, nd)
+    y = pd.hubbard_apply(h, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(y - yr) <= 64 * EPS32 * abs_bound(m, b, x) + 1e-30)
+    h.close()
+
+
+def test_hv_no_bonds_is_diagonal(env):
+    torch, pd = env
+    cl = wl.Cluster("isolated6", 6, (), ())
+    b = Basis(6, 3, 2)
+    x = start_vector(9, b.D)
+    h = pd.Handle(6, [], [], 3.0, 3, 2)
+    y = pd.hubbard_apply(h, torch.from_numpy(x).cuda()).cpu().numpy()
+    up, dn = b.split(b.combined)
+    docc = np.array([bin(int(u) & int(d)).count("1") for u, d in zip(up, dn)])
+    assert np.array_equal(y, 3.0 * docc * x)
+    h.close()
+
+
+def test_hv_rejects_aliasing_and_bad_sizes(env):
+    torch, pd = env
+    cl = wl.ring(6)
+    h = handle_for(cl, 1.0, 3, 3)
+    x = torch.zeros(h.D, dtype=torch.float64, device="cuda")
+    with pytest.raises(pd.HubbardError):
+        pd.hubbard_apply(h, x, x)
+    with pytest.raises(ValueError):
+        pd.hubbard_apply(h, torch.zeros(h.D + 1, dtype=torch.float64, device="cuda"))
+    h.close()
+
+
+def test_hv_hermitian_property(env):
+    """<x, H z> == <H x, z> on a mid-size cluster, on the GPU alone."""
+    torch, pd = env
+    cl = wl.rect_periodic(4, 3)
+    h = handle_for(cl, 5.0, 6, 5)
+    x = torch.from_numpy(start_vector(1, h.D)).cuda()
+    z = torch.from_numpy(start_vector(2, h.D)).cuda()
+    lhs = torch.dot(x, pd.hubbard_apply(h, z)).item()
+    rhs = torch.dot(pd.hubbard_apply(h, x), z).item()
+    assert abs(lhs - rhs) <= 1e-12 * x.norm().item() * z.norm().item() * 60
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def square4x4():
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    return cl, Model.from_cluster(cl, 8.0, 8, 8), Basis(16, 8, 8)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_hv_square4x4_full_size_sampled(env, square4x4, dtype):
+    """D = 165,636,900 in the benchmark's launch configuration: sampled outputs vs oracle rows."""
+    torch, pd = env
+    cl, m, b = square4x4
+    x = start_vector(0, b.D)
+    if dtype == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    h = handle_for(cl, 8.0, 8, 8)
+    xt = torch.from_numpy(x).cuda()
+    if dtype == "f32":
+        xt = xt.float()
+    y = pd.hubbard_apply(h, xt)
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.concatenate([[0, 1, b.D - 1, b.D - 2, 12869, 12870], rng.integers(0, b.D, 400)]))
+    ys = y[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    for r, yv in zip(rows, ys):
+        c, v = row(m, b, int(r))
+        ref = float(np.dot(v, x[c]))
+        bound = float(np.dot(np.abs(v), np.abs(x[c])))
+        eps = EPS64 if dtype == "f64" else EPS32
+        assert abs(yv - ref) <= 64 * eps * bound, (r, yv, ref)
+    h.close()
+
+
+def test_hv_square4x4_full_vector_vs_tensor_product_oracle(env, square4x4):
+    """Whole-vector comparison at full size against the oracle's tensor-product operator."""
+    torch, pd = env
+    cl, m, b = square4x4
+    k = KronOperator(m)
+    x = start_vector(5, k.D)
+    yr = k(x)
+    h = handle_for(cl, 8.0, 8, 8)
+    y = pd.hubbard_apply(h, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.max(np.abs(y - yr)) <= 1e-12 * np.max(np.abs(yr))
+    h.close()

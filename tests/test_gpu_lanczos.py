@@ -1,0 +1,142 @@
+"""GPU Lanczos ground states vs the oracle (E0 within 1e-10 relative, max(1,|E0|))."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle.basis import Basis
+from oracle.hamiltonian import KronOperator, Model, dense
+from oracle.lanczos import lanczos, start_vector
+from tests.conftest import GOLDEN
+from tests.gpu_util import handle_for, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    return torch, pd
+
+
+def golden(key):
+    p = os.path.join(GOLDEN, "oracle_energies.json")
+    if not os.path.exists(p):
+        pytest.skip("oracle energies not generated")
+    d = json.load(open(p))
+    if key not in d:
+        pytest.skip(f"{key} not in oracle energies")
+    return d[key]
+
+
+def close(a, b, tol=1e-10):
+    return abs(a - b) <= tol * max(1.0, abs(b))
+
+
+def test_ring8_full_reorth_100_steps(env):
+    """Ring of 8, (4,4), U=4, seeded start, 100 steps with full reorthogonalisation."""
+    torch, pd = env
+    cl = wl.ring(8)
+    m = Model.from_cluster(cl, 4.0, 4, 4)
+    b = Basis(8, 4, 4)
+    e_dense = float(np.linalg.eigvalsh(dense(m, b))[0])
+    h = handle_for(cl, 4.0, 4, 4)
+    r = pd.lanczos_ground_state(h, maxit=100, tol=0.0, reorth=True, seed=0)
+    assert r.iterations == 100
+    assert close(r.E0, e_dense)
+    # same start vector, same recurrence: alpha/beta agree with the oracle's iteration step by step
+    ro = lanczos(KronOperator(m), start_vector(0, b.D), 100, reorth=True, tol=None)
+    n = 30
+    assert np.allclose(r.alphas[:n], ro.alphas[:n], rtol=0, atol=1e-9)
+    assert np.allclose(r.betas[:n], ro.betas[:n], rtol=0, atol=1e-9)
+    h.close()
+
+
+def test_ring8_three_term_to_tolerance(env):
+    torch, pd = env
+    cl = wl.ring(8)
+    h = handle_for(cl, 4.0, 4, 4)
+    r = pd.lanczos_ground_state(h, maxit=400, tol=1e-10)
+    assert r.converged and r.residual <= 1e-10 * max(1, abs(r.E0))
+    assert close(r.E0, golden("ring8_U4_4_4")["E0"])
+    h.close()
+
+
+def test_ring8_mixed_precision_finish(env):
+    torch, pd = env
+    cl = wl.ring(8)
+    h = handle_for(cl, 4.0, 4, 4)
+    r = pd.lanczos_ground_state(h, maxit=400, tol=1e-10, dtype=torch.float32, fp64_finish=True)
+    assert r.converged and r.iterations_f32 > 0 and r.iterations > r.iterations_f32
+    assert close(r.E0, golden("ring8_U4_4_4")["E0"])
+    h.close()
+
+
+def test_float32_only_error_is_reported_scale(env):
+    """Float32 vectors without the float64 finish: E0 good to ~1e-6 relative, not 1e-10."""
+    torch, pd = env
+    cl = wl.ring(8)
+    h = handle_for(cl, 4.0, 4, 4)
+    r = pd.lanczos_ground_state(h, maxit=200, tol=1e-6, dtype=torch.float32)
+    e = golden("ring8_U4_4_4")["E0"]
+    assert abs(r.E0 - e) <= 1e-5 * abs(e)
+    h.close()
+
+
+def test_start_vector_argument_matches_seeded_start(env):
+    torch, pd = env
+    cl = wl.ring(8)
+    h = handle_for(cl, 4.0, 4, 4)
+    v0 = torch.from_numpy(start_vector(3, h.D)).cuda()
+    r1 = pd.lanczos_ground_state(h, maxit=30, tol=0.0, seed=3)
+    r2 = pd.lanczos_ground_state(h, maxit=30, tol=0.0, v0=v0)
+    assert np.allclose(r1.alphas, r2.alphas, rtol=0, atol=1e-12)
+    h.close()
+
+
+@pytest.mark.parametrize("cl,nu,nd,U", [(wl.dimer(), 1, 1, 4.0), (wl.ring(6), 6, 6, 2.0), (wl.ring(6), 0, 0, 2.0)])
+def test_degenerate_sizes(env, cl, nu, nd, U):
+    """D = 1 or tiny: the Krylov space is exhausted and the answer is exact."""
+    torch, pd = env
+    m = Model.from_cluster(cl, U, nu, nd)
+    e = float(np.linalg.eigvalsh(dense(m, Basis(cl.L, nu, nd)))[0])
+    h = handle_for(cl, U, nu, nd)
+    r = pd.lanczos_ground_state(h, maxit=50, tol=1e-10)
+    assert r.converged and close(r.E0, e, 1e-12)
+    h.close()
+
+
+def test_batch_instances_sample(env):
+    torch, pd = env
+    recs = golden("batch64")
+    insts = wl.draw_batch_instances(64)
+    for k in (0, 1, 7, 33, 63):
+        inst, rec = insts[k], recs[k]
+        h = handle_for(inst.cluster, inst.U, inst.N_up, inst.N_dn)
+        r = pd.lanczos_ground_state(h, maxit=2000, tol=1e-10, seed=inst.seed)
+        assert close(r.E0, rec["E0"]), (k, r.E0, rec["E0"])
+        h.close()
+
+
+def test_square4x4_f64_ground_state(env):
+    """4x4 t-t' cluster, U=8, half filling, float64 Lanczos to 1e-10 vs the oracle's Lanczos."""
+    torch, pd = env
+    rec = golden("square4x4_tp-0.3_U8_8_8")
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    h = handle_for(cl, 8.0, 8, 8)
+    r = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0)
+    assert r.converged and close(r.E0, rec["E0"])
+    h.close()
+
+
+def test_square4x4_mixed_precision_ground_state(env):
+    torch, pd = env
+    rec = golden("square4x4_tp-0.3_U8_8_8")
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    h = handle_for(cl, 8.0, 8, 8)
+    r = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0, dtype=torch.float32, fp64_finish=True)
+    assert r.converged and close(r.E0, rec["E0"])
+    h.close()

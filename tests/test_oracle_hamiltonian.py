@@ -110,3 +110,29 @@ def test_basis_vector_gives_row():
         nz = np.nonzero(col)[0]
         assert nz.tolist() == cols.tolist()
         assert np.array_equal(col[nz], vals)
+
+
+def test_abs_apply_is_entrywise_absolute_product():
+    cl = wl.rect_periodic(3, 3, 1.0, -0.3)
+    m = Model.from_cluster(cl, 3.0, 4, 3)
+    b = Basis(9, 4, 3)
+    x = start_vector(2, b.D)
+    want = np.abs(dense(m, b)) @ np.abs(x) if b.D <= 6000 else None
+    got = KronOperator(m, use_c=False).abs_apply(x)
+    if want is None:
+        # row by row from the canonical rows
+        for r in range(0, b.D, 997):
+            c, v = row(m, b, r)
+            assert abs(got[r] - np.dot(np.abs(v), np.abs(x[c]))) <= 1e-13 * got[r]
+    else:
+        assert np.allclose(got, want, rtol=1e-13, atol=0)
+
+
+def test_apply_rows_matches_apply():
+    from oracle.hamiltonian import apply_rows
+    cl = wl.rect_periodic(4, 3)
+    m = Model.from_cluster(cl, 5.0, 5, 4)
+    b = Basis(12, 5, 4)
+    x = start_vector(6, b.D)
+    rows = np.array([0, 5, 777, b.D - 1])
+    assert np.array_equal(apply_rows(m, b, x, rows), apply(m, b, x)[rows])
