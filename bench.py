@@ -182,6 +182,8 @@ def run_ours(args, world, rank, local):
         e0 = e1 = None
         if timed:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)  # materialise the CUDA events; the library re-records them around H·v
+            e1.record(stream)
             ev_hv.append((e0, e1))
         pd.lanczos_step(h, V[iv], vprev, V[iw], bprev, alpha[j:j + 1], beta[j:j + 1], scratch, e0, e1,
                         launches if timed else None)
