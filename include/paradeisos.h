@@ -188,6 +188,38 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
                        void *ev_hv_end, uint32_t *launches, void *stream);
 
 /*
+ * lanczos_step without any allocation (the paper has no counterpart; this is a
+ * deployment convenience).  Some callers cannot call cudaMalloc at the point
+ * where they step the solver: a host program that hands out all device memory
+ * through its own pool and forbids libraries from allocating behind its back,
+ * a plug-in that runs inside another framework's memory budget, or a loop that
+ * must not risk an allocation's latency or failure mid-run.  For them this
+ * entry point takes the same arguments as lanczos_step minus the scratch
+ * buffer: the reductions' partial sums live in a fixed device array inside the
+ * library, 2048 doubles (16 KiB), which every GPU that loads the library holds
+ * until the process exits.
+ *   - The caller still owns and passes v, vprev, w and the scalars.
+ *   - The handle's per-spin tables must already exist (any earlier
+ *     hubbard_apply, hubbard_row_entries, lanczos_step or lanczos_ground_state
+ *     on the handle builds them); otherwise HB_ERR_INVALID_STATE, because
+ *     building them would allocate.
+ *   - Call it with the handle's device current (else HB_ERR_INVALID_ARG).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture begins.
+ *   - A device whose reductions need more than 2048 partial sums (more than
+ *     512 SMs) is rejected with HB_ERR_NO_MEMORY.
+ *   - All calls on a device share the array, which keeps the last call's
+ *     contents (nothing in it needs to start at zero: every slot is written
+ *     before it is read).  Calls whose kernels overlap on the GPU race on it:
+ *     serialise them (one stream, or events).
+ * Neither this call nor anything it calls allocates or frees device memory.
+ */
+hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w,
+                               const double *beta_prev, double *alpha, double *beta, void *ev_hv_begin,
+                               void *ev_hv_end, uint32_t *launches, void *stream);
+
+/*
  * Host utility (no GPU needed): lowest eigenvalue theta of the symmetric
  * tridiagonal matrix with diagonal alpha[0..n) and off-diagonal beta[0..n-1),
  * by Sturm-sequence bisection, and the last component of its normalised

@@ -69,6 +69,7 @@ def load():
         "hb_tridiag_lowest": (ctypes.c_int, [P, P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "lanczos_step_scratch_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
         "lanczos_step": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, U64, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
+        "lanczos_step_noalloc": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -285,6 +286,19 @@ def lanczos_step(h: Handle, v, vprev, w, beta_prev, alpha, beta, scratch, ev_hv_
                                _ptr(scratch), scratch.numel() * scratch.element_size(), ev0, ev1,
                                ctypes.byref(launches) if launches is not None else None, _stream_ptr(stream)),
            "lanczos_step")
+
+
+def lanczos_step_noalloc(h: Handle, v, vprev, w, beta_prev, alpha, beta, ev_hv_begin=None, ev_hv_end=None,
+                         launches: Optional[ctypes.c_uint32] = None, stream=None):
+    """lanczos_step with the reductions' scratch in the library's fixed device array (no allocation)."""
+    _need_cuda(v, w)
+    code = _dtype_code(v)
+    ev0 = ctypes.c_void_p(ev_hv_begin.cuda_event) if ev_hv_begin is not None else ctypes.c_void_p(0)
+    ev1 = ctypes.c_void_p(ev_hv_end.cuda_event) if ev_hv_end is not None else ctypes.c_void_p(0)
+    _check(load().lanczos_step_noalloc(h.ptr, code, _ptr(v), _ptr(vprev), _ptr(w), _ptr(beta_prev), _ptr(alpha),
+                                       _ptr(beta), ev0, ev1,
+                                       ctypes.byref(launches) if launches is not None else None,
+                                       _stream_ptr(stream)), "lanczos_step_noalloc")
 
 
 def hb_tridiag_lowest(alpha, beta):

@@ -1,0 +1,66 @@
+"""The allocation-free Lanczos step against the regular one (GPU).
+
+Callers that may not allocate device memory while they step the solver use
+lanczos_step_noalloc, whose reduction scratch is a fixed array inside the
+library.  This file is collected last so that a failure here comes after every
+other test has run; it must pass alone in a fresh process as well.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle.lanczos import start_vector
+from tests.gpu_util import handle_for, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype_name", ["float64", "float32"])
+def test_noalloc_step_matches_regular_step_twice(dtype_name):
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    dtype = getattr(torch, dtype_name)
+    tol = 1e-12 if dtype_name == "float64" else 1e-5
+    cl = wl.rect_periodic(4, 3)
+    h = handle_for(cl, 5.0, 5, 4)
+    dev = torch.device("cuda")
+    v0 = torch.from_numpy(start_vector(21, h.D)).to(dev, dtype)
+    v0 /= v0.norm()
+    pd.hubbard_apply(h, v0)  # builds the handle's tables (the no-alloc call does not)
+    scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device=dev)
+
+    def run(no_alloc):
+        V = [v0.clone(), torch.empty_like(v0), torch.empty_like(v0)]
+        a = torch.zeros(2, dtype=torch.float64, device=dev)
+        b = torch.zeros(2, dtype=torch.float64, device=dev)
+        for j in range(2):  # two calls in a row: the second reuses the first call's scratch contents
+            vprev = V[(j - 1) % 3] if j > 0 else None
+            bprev = b[j - 1:j] if j > 0 else None
+            if no_alloc:
+                pd.lanczos_step_noalloc(h, V[j % 3], vprev, V[(j + 1) % 3], bprev, a[j:j + 1], b[j:j + 1])
+            else:
+                pd.lanczos_step(h, V[j % 3], vprev, V[(j + 1) % 3], bprev, a[j:j + 1], b[j:j + 1], scratch)
+        torch.cuda.synchronize()
+        return V[1].double().cpu().numpy(), V[2].double().cpu().numpy(), a.cpu().numpy(), b.cpu().numpy()
+
+    ref = run(False)
+    got = run(True)
+    for r, g in zip(ref, got):
+        assert np.max(np.abs(g - r)) <= tol * max(1.0, np.max(np.abs(r)))
+    assert pd.hubbard_last_error(h) == "HB_OK"
+    h.close()
+
+
+def test_noalloc_step_refuses_to_build_tables():
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    h = handle_for(wl.ring(6), 2.0, 3, 3)
+    v = torch.zeros(h.D, dtype=torch.float64, device="cuda")
+    v[0] = 1.0
+    w = torch.empty_like(v)
+    a = torch.zeros(1, dtype=torch.float64, device="cuda")
+    b = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(pd.HubbardError) as e:
+        pd.lanczos_step_noalloc(h, v, None, w, None, a, b)
+    assert e.value.name == "HB_ERR_INVALID_STATE"
+    h.close()
