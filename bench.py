@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="hubbard4x4_half", choices=sorted(WORKLOADS))
+    p.add_argument("--dtype", default="f64", choices=["f64", "fx64", "f32"],
+                   help="Krylov vector type: float64 (float64 FMAs), fixed-point int64, float32")
     p.add_argument("--no-solve", action="store_true", help="skip the time-to-E0 runs")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return p.parse_args()
@@ -162,9 +164,14 @@ def run_ours(args, world, rank, local):
     # inputs: a normalised random start vector (plumbing, outside the timed region)
     g = torch.Generator(device=dev)
     g.manual_seed(1234 + rank)
-    V = [torch.empty(D, dtype=torch.float64, device=dev) for _ in range(3)]
-    V[0].uniform_(-1.0, 1.0, generator=g)
-    V[0] /= V[0].norm()
+    vdt = {"f64": torch.float64, "fx64": torch.int64, "f32": torch.float32}[args.dtype]
+    x0 = torch.empty(D, dtype=torch.float64, device=dev)
+    x0.uniform_(-1.0, 1.0, generator=g)
+    x0 /= x0.norm()
+    if args.dtype == "fx64":
+        x0 = pd.hubbard_convert(h, x0, torch.int64)
+    V = [x0.to(vdt), torch.empty(D, dtype=vdt, device=dev), torch.empty(D, dtype=vdt, device=dev)]
+    del x0
     nsteps = args.warmup + args.steps
     alpha = torch.zeros(nsteps + 1, dtype=torch.float64, device=dev)
     beta = torch.zeros(nsteps + 1, dtype=torch.float64, device=dev)
@@ -217,7 +224,7 @@ def run_ours(args, world, rank, local):
 
     # end to end through the public API with host buffers: every step copies its input vector
     # from pinned host memory and reads alpha, beta back to the host
-    host_v = torch.empty(D, dtype=torch.float64, pin_memory=True)
+    host_v = torch.empty(D, dtype=vdt, pin_memory=True)
     host_v.copy_(V[nsteps % 3])
     host_ab = torch.empty(2, dtype=torch.float64, pin_memory=True)
     e2e_steps = max(3, min(args.steps, 10))
@@ -236,9 +243,10 @@ def run_ours(args, world, rank, local):
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_ms = float(e2e_t.item())
+    host_bytes = host_v.element_size()
 
     solve = None
-    if not args.no_solve and rank == 0 and args.workload == "hubbard4x4_half":
+    if not args.no_solve and rank == 0 and args.workload == "hubbard4x4_half" and args.dtype == "f64":
         solve = time_to_e0(pd, h, torch)
     del V, host_v
     h.close()
@@ -251,20 +259,24 @@ def run_ours(args, world, rank, local):
 
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs") if peaks else 6800.0
-    achieved = HV_BYTES_PER_STATE * D / (hv_ms * 1e-3) / 1e9
-    traffic = ncu_traffic("k_hv<2,double,true>")
+    bps = HV_BYTES_PER_STATE if args.dtype != "f32" else 8
+    achieved = bps * D / (hv_ms * 1e-3) / 1e9
+    kname = {"f64": "k_hv<2,double,true>", "fx64": "k_hv_fx<2,2,true>", "f32": "k_hv<4,float,true>"}[args.dtype]
+    traffic = ncu_traffic(kname)
     out = {
         "metric": METRIC, "value": round(world * D / (ms * 1e-3) / 1e9, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random start vector)",
-        "config": {**WORKLOADS[args.workload], **COMMON},
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "fx64": "int64", "f32": "f32"}[args.dtype],
+        "data": "synthetic (seeded random start vector)",
+        "config": {**WORKLOADS[args.workload], **COMMON, "vector_dtype": args.dtype},
         "hv_ms": round(hv_ms, 4), "hv_gstates_per_s": round(D / (hv_ms * 1e-3) / 1e9, 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "k_hv<2,double,true>", "bytes_per_state": HV_BYTES_PER_STATE,
+                     "kernel": kname, "bytes_per_state": bps,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "e2e": {"value": round(world * D / (e2e_ms * 1e-3) / 1e9, 4), "unit": UNIT,
-                "h2d_bytes_per_step": D * 8, "d2h_bytes_per_step": 16},
+                "h2d_bytes_per_step": D * host_bytes, "d2h_bytes_per_step": 16},
         "gpu_launches": int(launches.value),
         "clocks": clk,
         "recurrence_sane": sane,
@@ -288,7 +300,9 @@ def time_to_e0(pd, h, torch):
         pass
     res = {}
     for name, kw in (("plain_f64", dict(dtype=torch.float64)),
-                     ("mixed_f32_f64finish", dict(dtype=torch.float32, fp64_finish=True))):
+                     ("fx64", dict(dtype=torch.int64)),
+                     ("mixed_f32_f64finish", dict(dtype=torch.float32, fp64_finish="f64")),
+                     ("mixed_f32_fx64finish", dict(dtype=torch.float32, fp64_finish="fx64"))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0, raise_on_error=False, **kw)

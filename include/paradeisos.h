@@ -53,8 +53,14 @@ typedef enum {
 } hb_status;
 
 typedef enum {
-    HB_F64 = 0, /* IEEE binary64 vectors */
-    HB_F32 = 1  /* IEEE binary32 vectors */
+    HB_F64 = 0,  /* IEEE binary64 vectors */
+    HB_F32 = 1,  /* IEEE binary32 vectors */
+    HB_FX64 = 2  /* signed 64-bit fixed point: element q stands for q * 2^-F, F from
+                    hubbard_fixed_point_bits(); |value| must stay below 1 on input to
+                    H·v.  Sums of hops are exact integer sums, each coefficient class is
+                    applied once per element with one rounding (2^-(F+1)); reductions
+                    are exact 128-bit integer sums.  Needs at most 4 distinct hopping
+                    amplitudes and at most 255 bonds (else HB_ERR_INVALID_ARG). */
 } hb_dtype;
 
 /* Human-readable name of a status code (static string). */
@@ -81,6 +87,13 @@ hb_status hubbard_basis_destroy(hb_handle h);
 hb_status hubbard_basis_dim(hb_handle h, uint64_t *D, uint64_t *D_up, uint64_t *D_dn);
 /* Change U (the interaction of Eq. 1) without rebuilding any table. */
 hb_status hubbard_set_U(hb_handle h, double U);
+/* Number of fractional bits F of the HB_FX64 format of this handle, chosen at
+ * creation so that 3 * max_r sum_c |H_rc| * 2^F < 2^62 (Lanczos vectors of norm
+ * <= 1 and their images under H fit without overflow). */
+hb_status hubbard_fixed_point_bits(hb_handle h, int32_t *F);
+/* Element-wise conversion between HB_F64 and HB_FX64 vectors of length n
+ * (round to nearest; the float64 values must satisfy |x| * 2^F < 2^62). */
+hb_status hubbard_convert(hb_handle h, hb_dtype from, const void *x, hb_dtype to, void *y, uint64_t n, void *stream);
 
 /*
  * Paradeisos forward map, batched (Eq. 3 and the combined index of Sec. III).
@@ -132,8 +145,9 @@ typedef struct {
     double tol;           /* stop when beta_j |s_last| <= tol * max(1, |theta|); <= 0: run maxit */
     uint64_t seed;        /* start vector when v0 == NULL: SplitMix64, element i = output i+1
                              of the stream seeded with `seed`, mapped to [-1, 1), normalised */
-    int32_t fp64_finish;  /* with vec_dtype HB_F32: after the binary32 phase stalls, form the
-                             Ritz vector and continue in binary64 until tol is met */
+    int32_t fp64_finish;  /* with vec_dtype HB_F32: after the binary32 phase reaches its own
+                             tolerance, form the Ritz vector and continue until tol is met,
+                             in binary64 vectors (1) or HB_FX64 vectors (2) */
     int32_t f32_tol_exp;  /* binary32 phase ends when the residual <= 10^f32_tol_exp * max(1,|theta|)
                              or stops improving (default -5 when 0) */
 } hb_lanczos_opts;

@@ -94,6 +94,41 @@ def row(model: Model, basis: Basis, r: int):
     return np.asarray(cols, dtype=np.int64)[order], np.asarray(vals, dtype=np.float64)[order]
 
 
+def row_by_counting(model: Model, r: int):
+    """Canonical row r for clusters too large to list (e.g. 18 sites at half filling).
+
+    Same terms as `row`; positions come from the counting definition of the
+    sorted order (`count_below` / `string_at`) instead of a stored list:
+    combined position = C(L, N_dn) * position_up + position_dn (the order of
+    the sorted combined integers, up string in the high bits).
+    """
+    import math
+
+    from .basis import count_below, string_at
+    L = model.L
+    D_dn = math.comb(L, model.N_dn)
+    pu, pd_ = divmod(int(r), D_dn)
+    up, dn = string_at(pu, L, model.N_up), string_at(pd_, L, model.N_dn)
+    cols = [int(r)]
+    vals = [model.U * bin(up & dn).count("1")]
+    for b in range(len(model.t)):
+        i, j = int(model.bonds[b, 0]), int(model.bonds[b, 1])
+        for spin in (0, 1):
+            s = up if spin == 0 else dn
+            if ((s >> i) & 1) == ((s >> j) & 1):
+                continue
+            s2 = s ^ ((1 << i) | (1 << j))
+            sign = -1.0 if bin(s & between_mask(i, j)).count("1") % 2 else 1.0
+            if spin == 0:
+                c = count_below(s2, L, model.N_up) * D_dn + pd_
+            else:
+                c = pu * D_dn + count_below(s2, L, model.N_dn)
+            cols.append(c)
+            vals.append(-model.t[b] * sign)
+    order = np.argsort(np.asarray(cols, dtype=np.int64), kind="stable")
+    return np.asarray(cols, dtype=np.int64)[order], np.asarray(vals, dtype=np.float64)[order]
+
+
 def apply(model: Model, basis: Basis, x: np.ndarray) -> np.ndarray:
     """y = H x for the whole basis, evaluated term by term of Eq. 1.
 

@@ -15,7 +15,7 @@ from typing import Optional, Sequence, Tuple
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libparadeisos.so")
 
-HB_F64, HB_F32 = 0, 1
+HB_F64, HB_F32, HB_FX64 = 0, 1, 2
 STATUS = {0: "HB_OK", 1: "HB_ERR_INVALID_ARG", 2: "HB_ERR_OVERFLOW", 3: "HB_ERR_INVALID_STATE",
           4: "HB_ERR_OUT_OF_RANGE", 5: "HB_ERR_NO_MEMORY", 6: "HB_ERR_CUDA", 7: "HB_ERR_NOT_CONVERGED",
           8: "HB_ERR_TIMEOUT"}
@@ -67,6 +67,8 @@ def load():
         "lanczos_ground_state": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, P, U64, P, P,
                                                 ctypes.POINTER(D), ctypes.POINTER(LanczosInfo), P]),
         "hb_tridiag_lowest": (ctypes.c_int, [P, P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "hubbard_fixed_point_bits": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "hubbard_convert": (ctypes.c_int, [P, I32, P, I32, P, U64, P]),
         "lanczos_step_scratch_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
         "lanczos_step": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, U64, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
         "lanczos_step_noalloc": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
@@ -183,12 +185,31 @@ def paradeisos_unrank(h: Handle, idx, states=None, stream=None):
 
 
 def _dtype_code(t):
+    """float64 -> HB_F64, float32 -> HB_F32, int64 -> HB_FX64 (fixed point)."""
     import torch
     if t.dtype == torch.float64:
         return HB_F64
     if t.dtype == torch.float32:
         return HB_F32
-    raise ValueError("vectors must be float64 or float32")
+    if t.dtype == torch.int64:
+        return HB_FX64
+    raise ValueError("vectors must be float64, float32 or int64 (fixed point)")
+
+
+def hubbard_fixed_point_bits(h: "Handle") -> int:
+    F = ctypes.c_int32()
+    _check(load().hubbard_fixed_point_bits(h.ptr, ctypes.byref(F)), "hubbard_fixed_point_bits")
+    return F.value
+
+
+def hubbard_convert(h: "Handle", x, out_dtype, stream=None):
+    """float64 <-> fixed-point (int64) conversion of a device vector."""
+    import torch
+    _need_cuda(x)
+    y = torch.empty(x.shape, dtype=out_dtype, device=x.device)
+    _check(load().hubbard_convert(h.ptr, _dtype_code(x), _ptr(x), _dtype_code(y), _ptr(y), x.numel(),
+                                  _stream_ptr(stream)), "hubbard_convert")
+    return y
 
 
 def hubbard_apply(h: Handle, x, y=None, stream=None):
@@ -239,9 +260,11 @@ def lanczos_ground_state(h: Handle, maxit: int = 300, tol: float = 1e-10, reorth
                          seed: int = 0, v0=None, check_every: int = 1, fp64_finish: bool = False,
                          f32_tol_exp: int = 0, workspace=None, stream=None, raise_on_error: bool = True) -> LanczosResult:
     import torch
-    dt = HB_F64 if dtype in (None, torch.float64) else HB_F32
+    dt = {None: HB_F64, torch.float64: HB_F64, torch.float32: HB_F32, torch.int64: HB_FX64}[dtype]
+    fin = {False: 0, True: 1, "f64": 1, "fx64": 2}[fp64_finish] if not isinstance(fp64_finish, int) or \
+        isinstance(fp64_finish, bool) else int(fp64_finish)
     o = LanczosOpts(int(maxit), int(bool(reorth)), dt, int(check_every), float(tol), int(seed) & ((1 << 64) - 1),
-                    int(bool(fp64_finish)), int(f32_tol_exp))
+                    fin, int(f32_tol_exp))
     lib = load()
     nb = ctypes.c_uint64()
     _check(lib.lanczos_workspace_bytes(h.ptr, ctypes.byref(o), ctypes.byref(nb)), "lanczos_workspace_bytes")

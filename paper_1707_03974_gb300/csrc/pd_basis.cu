@@ -6,6 +6,7 @@
 // (combined index I = C(L, N_dn) idx_up + idx_dn), Sec. II B (hops and the
 // fermion sign, double occupancy by AND).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <set>
@@ -126,6 +127,56 @@ __global__ void k_spin_hops(const uint32_t *__restrict__ g_lut, const uint32_t *
     }
 }
 
+// The same hops re-ordered for the fixed-point path: segments of equal
+// (amplitude class, sign), class-major, so that the H·v can add plain integers
+// and apply each class's amplitude once per element.
+__global__ void k_spin_hops_fx(const uint32_t *__restrict__ g_lut, const uint32_t *__restrict__ str, uint64_t D,
+                               const int32_t *__restrict__ bonds, const int32_t *__restrict__ bond_class,
+                               int n_bonds, uint32_t *__restrict__ ftarget, uint64_t *__restrict__ seg) {
+    __shared__ uint32_t lut[PD_LUT_W * PD_LUT_W];
+    load_lut(lut, g_lut);
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < D; r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = str[r];
+        int cnt[2 * PD_FX_MAXC] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int b = 0; b < n_bonds; ++b) {
+            const int i = bonds[2 * b], j = bonds[2 * b + 1];
+            if (((s >> i) & 1u) == ((s >> j) & 1u)) continue;
+            const int lo = min(i, j), hi = max(i, j);
+            const uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
+            const int neg = __popc(s & between) & 1;
+            ++cnt[2 * bond_class[b] + neg];
+        }
+        int off[2 * PD_FX_MAXC];
+        uint64_t packed = 0;
+        int acc = 0;
+        for (int q = 0; q < 2 * PD_FX_MAXC; ++q) {
+            off[q] = acc;
+            acc += cnt[q];
+            packed |= (uint64_t)cnt[q] << (8 * q);
+        }
+        seg[r] = packed;
+        for (int b = 0; b < n_bonds; ++b) {
+            const int i = bonds[2 * b], j = bonds[2 * b + 1];
+            if (((s >> i) & 1u) == ((s >> j) & 1u)) continue;
+            const int lo = min(i, j), hi = max(i, j);
+            const uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
+            const int neg = __popc(s & between) & 1;
+            const int q = 2 * bond_class[b] + neg;
+            ftarget[(uint64_t)(off[q]++) * D + r] = pd_forward_map(lut, s ^ ((1u << i) | (1u << j)));
+        }
+    }
+}
+
+__global__ void k_f64_to_fx(const double *__restrict__ x, int64_t *__restrict__ y, uint64_t n, int F) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        y[i] = __double2ll_rn(ldexp(x[i], F));
+}
+
+__global__ void k_fx_to_f64(const int64_t *__restrict__ x, double *__restrict__ y, uint64_t n, int F) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        y[i] = ldexp((double)x[i], -F);
+}
+
 // One thread per exported row: diagonal, spin-up hops (u' , d), spin-down hops
 // (u, d'), sorted by column (insertion sort; rows hold at most 1 + 2 n_bonds).
 __global__ void k_row_entries(uint64_t row0, uint32_t nrows, uint32_t max_entries, double U, uint64_t D_dn,
@@ -196,6 +247,8 @@ void free_spin(SpinTables &s) {
     cudaFree(s.target);
     cudaFree(s.val);
     cudaFree(s.valf);
+    cudaFree(s.ftarget);
+    cudaFree(s.seg);
     s = SpinTables();
 }
 
@@ -223,13 +276,82 @@ hb_status build_spin(hb_handle h, SpinTables &st, int n) {
     k_spin_hops<<<grid_for(D, h->sm_count), kThreads>>>(h->d_binom, st.str, D, h->d_bonds, h->d_t, h->n_bonds,
                                                         st.target, st.val, st.valf);
     PD_CUDA(cudaGetLastError());
+    if (h->fx_ok) {
+        if (cudaMalloc(&st.ftarget, ne * sizeof(uint32_t)) != cudaSuccess) return HB_ERR_NO_MEMORY;
+        if (cudaMalloc(&st.seg, D * sizeof(uint64_t)) != cudaSuccess) return HB_ERR_NO_MEMORY;
+        k_spin_hops_fx<<<grid_for(D, h->sm_count), kThreads>>>(h->d_binom, st.str, D, h->d_bonds, h->d_bond_class,
+                                                               h->n_bonds, st.ftarget, st.seg);
+        PD_CUDA(cudaGetLastError());
+    }
     PD_CUDA(cudaDeviceSynchronize());
     return HB_OK;
 }
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Reverse Cuthill-McKee order of the spin-up hop graph (breadth-first from the
+// lowest-degree unvisited string, neighbours in order of increasing degree,
+// the whole order reversed).  Only changes the order in which rows are
+// visited, never the storage order of vectors.
+hb_status build_row_order(hb_handle h) {
+    const uint64_t n = h->D_up;
+    const int z = h->up.zmax;
+    std::vector<uint16_t> cnt(n);
+    std::vector<uint32_t> tgt((uint64_t)std::max(z, 1) * n);
+    PD_CUDA(cudaMemcpy(cnt.data(), h->up.count, n * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    if (z > 0) PD_CUDA(cudaMemcpy(tgt.data(), h->up.target, (uint64_t)z * n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> by_degree(n);
+    for (uint64_t i = 0; i < n; ++i) by_degree[i] = (uint32_t)i;
+    std::stable_sort(by_degree.begin(), by_degree.end(), [&](uint32_t a, uint32_t b) { return cnt[a] < cnt[b]; });
+    std::vector<uint8_t> seen(n, 0);
+    std::vector<uint32_t> order;
+    order.reserve(n);
+    std::vector<uint32_t> nb;
+    for (uint32_t start : by_degree) {
+        if (seen[start]) continue;
+        seen[start] = 1;
+        uint64_t head = order.size();
+        order.push_back(start);
+        while (head < order.size()) {
+            const uint32_t u = order[head++];
+            nb.clear();
+            for (int k = 0; k < cnt[u]; ++k) {
+                const uint32_t v = tgt[(uint64_t)k * n + u];
+                if (!seen[v]) {
+                    seen[v] = 1;
+                    nb.push_back(v);
+                }
+            }
+            std::stable_sort(nb.begin(), nb.end(), [&](uint32_t a, uint32_t b) { return cnt[a] < cnt[b]; });
+            order.insert(order.end(), nb.begin(), nb.end());
+        }
+    }
+    std::reverse(order.begin(), order.end());
+    if (cudaMalloc(&h->d_row_order, n * sizeof(uint32_t)) != cudaSuccess) return HB_ERR_NO_MEMORY;
+    PD_CUDA(cudaMemcpy(h->d_row_order, order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    return HB_OK;
+}
+
 }  // namespace
+
+static FxCoef fx_coef_host(double c) {
+    FxCoef r;
+    if (c == 0.0) return r;
+    int e = 0;
+    std::frexp(c, &e);
+    int G = 62 - e;
+    G = G < 1 ? 1 : (G > 63 ? 63 : G);
+    r.G = G;
+    r.K = std::llround(std::ldexp(c, G));
+    return r;
+}
+
+hb_status pd_fx_coefs(hb_handle h, FxCoef *diag, FxCoef *cls) {
+    if (!h->fx_ok) return HB_ERR_INVALID_ARG;
+    for (int k = 0; k <= PD_MAXL; ++k) diag[k] = fx_coef_host(h->U * (double)k);
+    for (int c = 0; c < PD_FX_MAXC; ++c) cls[c] = fx_coef_host(c < h->n_classes ? -h->class_t[c] : 0.0);
+    return HB_OK;
+}
 
 void pd_record_error(hb_handle h, hb_status s) {
     unsigned bit = PD_ERRBIT(s);
@@ -253,8 +375,11 @@ hb_status pd_build_tables(hb_handle h) {
             s = build_spin(h, h->dn, h->N_dn);
         }
     }
+    if (s == HB_OK && h->D_up <= (1ull << 26)) s = build_row_order(h);
     if (dev_now != h->device) cudaSetDevice(dev_now);
     if (s != HB_OK) {
+        cudaFree(h->d_row_order);
+        h->d_row_order = nullptr;
         free_spin(h->up);
         if (!h->same_spin_tables) free_spin(h->dn);
         h->dn = SpinTables();
@@ -336,6 +461,38 @@ hb_status hubbard_basis_create(int L, int n_bonds, const int32_t *bonds, const d
         return fail(HB_ERR_CUDA);
     if (cudaMemcpy(h->d_t, h->h_t, sizeof(double) * nb, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(HB_ERR_CUDA);
+    // fixed-point format: amplitude classes (distinct t values) and fractional bits F
+    {
+        std::vector<int32_t> cls(nb, 0);
+        int nc = 0;
+        bool ok = n_bonds <= 255;
+        for (int b = 0; b < n_bonds && ok; ++b) {
+            int c = 0;
+            while (c < nc && h->class_t[c] != t[b]) ++c;
+            if (c == nc) {
+                if (nc == PD_FX_MAXC) {
+                    ok = false;
+                    break;
+                }
+                h->class_t[nc++] = t[b];
+            }
+            cls[b] = c;
+        }
+        h->fx_ok = ok;
+        h->n_classes = ok ? nc : 0;
+        double bound = std::fabs(U) * (double)std::min(N_up, N_dn);
+        double tsum = 0.0;
+        for (int b = 0; b < n_bonds; ++b) tsum += std::fabs(t[b]);
+        bound += 2.0 * tsum;
+        int F = 60;
+        const double lim1 = 3.0 * std::max(bound, 1.0);      // |w| <= 3 max row sum of |H|
+        const double lim2 = 2.0 * n_bonds + 1.0;              // class sums of inputs below 1
+        while (F > 8 && (std::ldexp(std::max(lim1, lim2), F) >= std::ldexp(1.0, 62))) --F;
+        h->fx_frac = F;
+        if (cudaMalloc(&h->d_bond_class, sizeof(int32_t) * nb) != cudaSuccess) return fail(HB_ERR_CUDA);
+        if (cudaMemcpy(h->d_bond_class, cls.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(HB_ERR_CUDA);
+    }
     if (cudaMalloc(&h->d_err, sizeof(unsigned)) != cudaSuccess) return fail(HB_ERR_CUDA);
     if (cudaMemset(h->d_err, 0, sizeof(unsigned)) != cudaSuccess) return fail(HB_ERR_CUDA);
     *out = h;
@@ -350,6 +507,8 @@ hb_status hubbard_basis_destroy(hb_handle h) {
     cudaFree(h->d_bonds);
     cudaFree(h->d_t);
     cudaFree(h->d_err);
+    cudaFree(h->d_bond_class);
+    cudaFree(h->d_row_order);
     delete[] h->h_bonds;
     delete[] h->h_t;
     delete h;
@@ -361,6 +520,27 @@ hb_status hubbard_basis_dim(hb_handle h, uint64_t *D, uint64_t *D_up, uint64_t *
     if (D) *D = h->D;
     if (D_up) *D_up = h->D_up;
     if (D_dn) *D_dn = h->D_dn;
+    return HB_OK;
+}
+
+hb_status hubbard_fixed_point_bits(hb_handle h, int32_t *F) {
+    if (!h || !F) return HB_ERR_INVALID_ARG;
+    *F = h->fx_frac;
+    return HB_OK;
+}
+
+hb_status hubbard_convert(hb_handle h, hb_dtype from, const void *x, hb_dtype to, void *y, uint64_t n, void *stream) {
+    if (!h || (n > 0 && (!x || !y))) return HB_ERR_INVALID_ARG;
+    if (n == 0) return HB_OK;
+    if (from == HB_F64 && to == HB_FX64)
+        k_f64_to_fx<<<grid_for(n, h->sm_count), kThreads, 0, as_stream(stream)>>>(
+            static_cast<const double *>(x), static_cast<int64_t *>(y), n, h->fx_frac);
+    else if (from == HB_FX64 && to == HB_F64)
+        k_fx_to_f64<<<grid_for(n, h->sm_count), kThreads, 0, as_stream(stream)>>>(
+            static_cast<const int64_t *>(x), static_cast<double *>(y), n, h->fx_frac);
+    else
+        return HB_ERR_INVALID_ARG;
+    PD_CUDA(cudaGetLastError());
     return HB_OK;
 }
 

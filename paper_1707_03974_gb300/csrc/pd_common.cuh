@@ -10,6 +10,8 @@
 #define PD_LUT_W (PD_MAXL + 1)  // binomial table is PD_LUT_W x PD_LUT_W
 #define PD_INVALID UINT64_MAX
 
+#define PD_FX_MAXC 4  // distinct hopping amplitudes supported by the fixed-point path
+
 // Sticky device error bits (one bit per hb_status code).
 #define PD_ERRBIT(s) (1u << (unsigned)(s))
 
@@ -33,6 +35,17 @@ struct SpinTables {
     uint32_t *target = nullptr;  // [zmax * D]
     double *val = nullptr;       // [zmax * D]
     float *valf = nullptr;       // [zmax * D] binary32 copy of val
+    // fixed-point path: the same hops re-ordered by (amplitude class, sign),
+    // ftarget[k * D + r]; seg[r] packs the 2*PD_FX_MAXC segment lengths as bytes
+    // (class c, sign +) at byte 2c and (class c, sign -) at byte 2c+1.
+    uint32_t *ftarget = nullptr;
+    uint64_t *seg = nullptr;
+};
+
+// A real multiplier c in fixed point: c ~ K * 2^-G with |K| < 2^62, 1 <= G <= 63.
+struct FxCoef {
+    int64_t K = 0;
+    int G = 1;
 };
 
 struct hb_basis {
@@ -48,14 +61,48 @@ struct hb_basis {
     bool tables_built = false;
     bool same_spin_tables = false;  // N_up == N_dn: dn tables alias up tables
     SpinTables up, dn;
+    // order in which the H·v visits the rows (spin-up strings): reverse
+    // Cuthill-McKee over the spin-up hop graph, so that rows processed close in
+    // time share hop neighbours and their x rows are still in L2
+    uint32_t *d_row_order = nullptr;  // [D_up]
     int32_t *h_bonds = nullptr;
     double *h_t = nullptr;
+    // fixed-point (HB_FX64) support
+    bool fx_ok = false;          // <= PD_FX_MAXC distinct amplitudes and <= 255 bonds
+    int fx_frac = 0;             // F: element q stands for q * 2^-F
+    int n_classes = 0;
+    double class_t[PD_FX_MAXC] = {0, 0, 0, 0};
+    int32_t *d_bond_class = nullptr;  // [n_bonds]
 };
 
 // ---- internal entry points shared between translation units ----
 hb_status pd_build_tables(hb_handle h);
 hb_status pd_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st);
 void pd_record_error(hb_handle h, hb_status s);
+
+hb_status pd_fx_coefs(hb_handle h, FxCoef *diag /*[PD_MAXL+1]*/, FxCoef *cls /*[PD_FX_MAXC]*/);
+
+// Fixed-point multiply with rounding to nearest: round(a * K / 2^G), 1 <= G <= 63.
+__device__ __forceinline__ int64_t fx_mul(int64_t a, int64_t K, int G) {
+    int64_t hi = __mul64hi(a, K);
+    const uint64_t lo = (uint64_t)a * (uint64_t)K;
+    const uint64_t lo2 = lo + (1ull << (G - 1));
+    hi += (lo2 < lo) ? 1 : 0;
+    return (int64_t)((lo2 >> G) | ((uint64_t)hi << (64 - G)));
+}
+
+// Multiplier for a float64 value (device side, used for alpha, beta, 1/beta).
+__device__ __forceinline__ FxCoef fx_coef_dev(double c) {
+    FxCoef r;
+    if (c == 0.0 || !(c == c)) return r;
+    int e = 0;
+    frexp(c, &e);
+    int G = 62 - e;
+    G = G < 1 ? 1 : (G > 63 ? 63 : G);
+    r.G = G;
+    r.K = __double2ll_rn(ldexp(c, G));
+    return r;
+}
 
 // Binomial C(i, m) from a table laid out as above (0 when m > i).
 __device__ __forceinline__ uint32_t pd_binom(const uint32_t *lut, int i, int m) {

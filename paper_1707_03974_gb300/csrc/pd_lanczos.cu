@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "pd_common.cuh"
@@ -209,6 +210,147 @@ __global__ void k_copy(const T *__restrict__ a, T *__restrict__ b, uint64_t n) {
         b[i] = a[i];
 }
 
+// ---------------- fixed-point (HB_FX64) vector kernels ----------------
+// Dot products of fixed-point vectors are exact: each 64x64-bit product is
+// kept as a 128-bit integer and summed in 128 bits (per thread, per block and
+// across blocks, in a fixed order), then converted to float64 once.
+struct I128 {
+    uint64_t lo = 0;
+    int64_t hi = 0;
+};
+
+__device__ __forceinline__ void i128_add_prod(I128 &s, int64_t a, int64_t b) {
+    const int64_t ph = __mul64hi(a, b);
+    const uint64_t pl = (uint64_t)a * (uint64_t)b;
+    const uint64_t lo = s.lo + pl;
+    s.hi += ph + (lo < pl ? 1 : 0);
+    s.lo = lo;
+}
+
+__device__ __forceinline__ void i128_add(I128 &s, const I128 &t) {
+    const uint64_t lo = s.lo + t.lo;
+    s.hi += t.hi + (lo < t.lo ? 1 : 0);
+    s.lo = lo;
+}
+
+__device__ __forceinline__ I128 block_sum128(I128 v) {
+    __shared__ uint64_t s_lo[32];
+    __shared__ int64_t s_hi[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        I128 t;
+        t.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        t.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        i128_add(v, t);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        s_lo[wid] = v.lo;
+        s_hi[wid] = v.hi;
+    }
+    __syncthreads();
+    I128 r;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        if (lane < nw) {
+            r.lo = s_lo[lane];
+            r.hi = s_hi[lane];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            I128 t;
+            t.lo = __shfl_down_sync(0xffffffffu, r.lo, o);
+            t.hi = __shfl_down_sync(0xffffffffu, r.hi, o);
+            i128_add(r, t);
+        }
+    }
+    return r;  // valid in thread 0
+}
+
+// <a, b> with every 128-bit product shifted right by `sh` bits first, so that
+// vectors far from unit norm (a fresh start vector) cannot overflow 128 bits.
+__global__ void k_fx_dot(const int64_t *__restrict__ a, const int64_t *__restrict__ b, uint64_t n, int sh,
+                         I128 *__restrict__ partials) {
+    I128 acc;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t ph = __mul64hi(a[i], b[i]);
+        const uint64_t pl = (uint64_t)a[i] * (uint64_t)b[i];
+        I128 p;
+        p.lo = sh == 0 ? pl : ((pl >> sh) | ((uint64_t)ph << (64 - sh)));
+        p.hi = sh == 0 ? ph : (ph >> sh);
+        i128_add(acc, p);
+    }
+    const I128 s = block_sum128(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_fx_axpy_dot(int64_t *__restrict__ w, const int64_t *__restrict__ vprev,
+                              const double *__restrict__ beta_prev, const int64_t *__restrict__ v, uint64_t n,
+                              I128 *__restrict__ partials) {
+    I128 acc;
+    const FxCoef b = beta_prev ? fx_coef_dev(*beta_prev) : FxCoef();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        int64_t wi = w[i];
+        if (beta_prev) {
+            wi -= fx_mul(vprev[i], b.K, b.G);
+            w[i] = wi;
+        }
+        i128_add_prod(acc, wi, v[i]);
+    }
+    const I128 s = block_sum128(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_fx_axpy_norm(int64_t *__restrict__ w, const int64_t *__restrict__ v,
+                               const double *__restrict__ alpha, uint64_t n, I128 *__restrict__ partials) {
+    I128 acc;
+    const FxCoef al = fx_coef_dev(*alpha);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t wi = w[i] - fx_mul(v[i], al.K, al.G);
+        w[i] = wi;
+        i128_add_prod(acc, wi, wi);
+    }
+    const I128 s = block_sum128(acc);
+    if (partials && threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_fx_scale(int64_t *__restrict__ v, const double *__restrict__ den, uint64_t n) {
+    const double d = *den;
+    const FxCoef f = fx_coef_dev(d != 0.0 ? 1.0 / d : 0.0);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        v[i] = fx_mul(v[i], f.K, f.G);
+}
+
+// Exact 128-bit sum of block partials, converted once: value * 2^(sh - 2F); mode 1 takes the square root.
+__global__ void k_reduce128(const I128 *__restrict__ partials, int nb, double *__restrict__ out, int mode, int F,
+                            int sh = 0) {
+    I128 s;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) i128_add(s, partials[i]);
+    s = block_sum128(s);
+    if (threadIdx.x == 0) {
+        const double v = ldexp((double)s.hi * 18446744073709551616.0 + (double)s.lo, sh - 2 * F);
+        out[0] = mode == 1 ? sqrt(v) : v;
+    }
+}
+
+// Uniform [-1, 1) start vector in fixed point: SplitMix64 output k = z >> 11
+// stands for k * 2^-52 - 1 (exact when F >= 52).
+__global__ void k_fill_random_fx(int64_t *__restrict__ v, uint64_t n, uint64_t seed, int F) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (i + 1) * kGamma;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z = z ^ (z >> 31);
+        const int64_t k = (int64_t)(z >> 11);
+        const int64_t q = F >= 52 ? (k << (F - 52)) : ((k + (1ll << (51 - F))) >> (52 - F));
+        v[i] = q - (1ll << F);
+    }
+}
+
+__global__ void k_f32_to_fx(const float *__restrict__ a, int64_t *__restrict__ b, uint64_t n, int F) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        b[i] = __double2ll_rn(ldexp((double)a[i], F));
+}
+
 // ---------------- host: tridiagonal lowest eigenpair ----------------
 int sturm_below(const double *a, const double *b, int n, double x) {
     int c = 0;
@@ -323,8 +465,9 @@ Layout make_layout(hb_handle h, const hb_lanczos_opts &o) {
     L.maxit = o.maxit;
     const uint64_t D = h->D;
     L.nblk = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)h->sm_count * 4, (D + kRedThreads - 1) / kRedThreads));
-    const uint64_t npart = (uint64_t)L.nblk * (o.reorth ? (uint64_t)(o.maxit + 1) : 1ull);
-    const uint64_t es = o.vec_dtype == HB_F64 ? 8 : 4;
+    // 16 bytes per partial: a float64 sum, or a 128-bit integer sum for HB_FX64
+    const uint64_t npart = 2ull * L.nblk * (o.reorth ? (uint64_t)(o.maxit + 1) : 1ull);
+    const uint64_t es = o.vec_dtype == HB_F32 ? 4 : 8;
     L.partials = 0;
     L.scal = align256(npart * 8);
     // scalars: alpha[maxit+1], beta[maxit+1], coef[maxit+1], misc[8]
@@ -353,9 +496,18 @@ struct Solve {
 
 template <typename T>
 hb_status normalise(Solve &s, T *v) {
-    k_dot<T><<<s.nblk, kRedThreads, 0, s.st>>>(v, v, s.D, s.partials);
-    k_reduce<<<1, kFinalThreads, 0, s.st>>>(s.partials, s.nblk, s.d_misc, 1);
-    k_scale<T><<<s.grid_vec, kRedThreads, 0, s.st>>>(v, s.d_misc, s.D);
+    if constexpr (std::is_same<T, int64_t>::value) {
+        const int nb = s.nblk;
+        I128 *part = reinterpret_cast<I128 *>(s.partials);
+        // |v_i| < 2^62 and up to 2^33 elements: dropping 32 bits per product keeps the sum in 128 bits
+        k_fx_dot<<<nb, kRedThreads, 0, s.st>>>(v, v, s.D, 32, part);
+        k_reduce128<<<1, kFinalThreads, 0, s.st>>>(part, nb, s.d_misc, 1, s.h->fx_frac, 32);
+        k_fx_scale<<<s.grid_vec, kRedThreads, 0, s.st>>>(v, s.d_misc, s.D);
+    } else {
+        k_dot<T><<<s.nblk, kRedThreads, 0, s.st>>>(v, v, s.D, s.partials);
+        k_reduce<<<1, kFinalThreads, 0, s.st>>>(s.partials, s.nblk, s.d_misc, 1);
+        k_scale<T><<<s.grid_vec, kRedThreads, 0, s.st>>>(v, s.d_misc, s.D);
+    }
     PD_CUDA(cudaGetLastError());
     return HB_OK;
 }
@@ -376,6 +528,41 @@ hb_status three_term_step(Solve &s, hb_dtype dt, const T *v, const T *vp, T *w, 
     if (scale) k_scale<T><<<s.grid_vec, kRedThreads, 0, s.st>>>(w, beta, s.D);
     PD_CUDA(cudaGetLastError());
     return HB_OK;
+}
+
+hb_status three_term_step_fx(Solve &s, const int64_t *v, const int64_t *vp, int64_t *w, const double *beta_prev,
+                             double *alpha, double *beta, bool scale, cudaEvent_t ev0, cudaEvent_t ev1) {
+    const int nb = s.nblk;
+    I128 *part = reinterpret_cast<I128 *>(s.partials);
+    const int F = s.h->fx_frac;
+    if (ev0) PD_CUDA(cudaEventRecord(ev0, s.st));
+    hb_status st = pd_apply(s.h, HB_FX64, v, w, s.st);
+    if (st != HB_OK) return st;
+    if (ev1) PD_CUDA(cudaEventRecord(ev1, s.st));
+    k_fx_axpy_dot<<<nb, kRedThreads, 0, s.st>>>(w, vp, vp ? beta_prev : nullptr, v, s.D, part);
+    k_reduce128<<<1, kFinalThreads, 0, s.st>>>(part, nb, alpha, 0, F);
+    k_fx_axpy_norm<<<nb, kRedThreads, 0, s.st>>>(w, v, alpha, s.D, part);
+    k_reduce128<<<1, kFinalThreads, 0, s.st>>>(part, nb, beta, 1, F);
+    if (scale) k_fx_scale<<<s.grid_vec, kRedThreads, 0, s.st>>>(w, beta, s.D);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+template <typename T>
+hb_status step_any(Solve &s, hb_dtype dt, const T *v, const T *vp, T *w, const double *beta_prev, double *alpha,
+                   double *beta, bool scale, cudaEvent_t ev0, cudaEvent_t ev1) {
+    if constexpr (std::is_same<T, int64_t>::value)
+        return three_term_step_fx(s, v, vp, w, beta_prev, alpha, beta, scale, ev0, ev1);
+    else
+        return three_term_step<T>(s, dt, v, vp, w, beta_prev, alpha, beta, scale, ev0, ev1);
+}
+
+template <typename T>
+void scale_any(Solve &s, T *w, const double *den) {
+    if constexpr (std::is_same<T, int64_t>::value)
+        k_fx_scale<<<s.grid_vec, kRedThreads, 0, s.st>>>(w, den, s.D);
+    else
+        k_scale<T><<<s.grid_vec, kRedThreads, 0, s.st>>>(w, den, s.D);
 }
 
 struct PhaseResult {
@@ -399,9 +586,11 @@ hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, b
         T *w = V + (uint64_t)iw * stride;
         T *vp = ip >= 0 ? V + (uint64_t)ip * stride : nullptr;
         if (!reorth) {
-            hb_status st = three_term_step<T>(s, dt, v, vp, w, vp ? s.d_beta + (j - 1) : nullptr, s.d_alpha + j,
-                                              s.d_beta + j, false, nullptr, nullptr);
+            hb_status st = step_any<T>(s, dt, v, vp, w, vp ? s.d_beta + (j - 1) : nullptr, s.d_alpha + j,
+                                       s.d_beta + j, false, nullptr, nullptr);
             if (st != HB_OK) return st;
+        } else if constexpr (std::is_same<T, int64_t>::value) {
+            return HB_ERR_INVALID_ARG;  // full reorthogonalisation is float only
         } else {
             hb_status st = pd_apply(s.h, dt, v, w, s.st);
             if (st != HB_OK) return st;
@@ -444,7 +633,7 @@ hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, b
                 return HB_OK;
             }
         }
-        k_scale<T><<<s.grid_vec, kRedThreads, 0, s.st>>>(w, s.d_beta + j, s.D);
+        scale_any<T>(s, w, s.d_beta + j);
         if (reorth) {
             ip = iv;
             iv = j + 1;
@@ -475,19 +664,22 @@ hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes) {
     hb_lanczos_opts o{};
     o.maxit = 1;
     o.vec_dtype = HB_F64;
-    *bytes = (uint64_t)make_layout(h, o).nblk * sizeof(double);
+    *bytes = (uint64_t)make_layout(h, o).nblk * 16;  // one 16-byte partial per reduction block
     return HB_OK;
 }
 
 hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w, const double *beta_prev,
                        double *alpha, double *beta, void *scratch, uint64_t scratch_bytes, void *ev_hv_begin,
                        void *ev_hv_end, uint32_t *launches, void *stream) {
-    if (!h || !v || !w || !alpha || !beta || !scratch || (dt != HB_F64 && dt != HB_F32)) return HB_ERR_INVALID_ARG;
+    if (!h || !v || !w || !alpha || !beta || !scratch || (dt != HB_F64 && dt != HB_F32 && dt != HB_FX64))
+        return HB_ERR_INVALID_ARG;
     if ((vprev == nullptr) != (beta_prev == nullptr)) return HB_ERR_INVALID_ARG;
+    if (dt == HB_FX64 && !h->fx_ok) return HB_ERR_INVALID_ARG;
+    if ((uintptr_t)scratch % 16 != 0) return HB_ERR_INVALID_ARG;
     uint64_t need = 0;
     lanczos_step_scratch_bytes(h, &need);
     if (scratch_bytes < need) return HB_ERR_NO_MEMORY;
-    const size_t es = dt == HB_F64 ? 8 : 4;
+    const size_t es = dt == HB_F32 ? 4 : 8;
     const uintptr_t n = (uintptr_t)(h->D * es), wb = (uintptr_t)w;
     for (const void *p : {v, vprev}) {
         const uintptr_t pb = (uintptr_t)p;
@@ -499,13 +691,16 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
     s.h = h;
     s.st = reinterpret_cast<cudaStream_t>(stream);
     s.D = h->D;
-    s.nblk = (int)(need / sizeof(double));
+    s.nblk = (int)(need / 16);
     s.partials = static_cast<double *>(scratch);
     s.grid_vec = h->sm_count * 8;
     cudaEvent_t e0 = reinterpret_cast<cudaEvent_t>(ev_hv_begin), e1 = reinterpret_cast<cudaEvent_t>(ev_hv_end);
     if (dt == HB_F64)
         st = three_term_step<double>(s, dt, static_cast<const double *>(v), static_cast<const double *>(vprev),
                                      static_cast<double *>(w), beta_prev, alpha, beta, true, e0, e1);
+    else if (dt == HB_FX64)
+        st = three_term_step_fx(s, static_cast<const int64_t *>(v), static_cast<const int64_t *>(vprev),
+                                static_cast<int64_t *>(w), beta_prev, alpha, beta, true, e0, e1);
     else
         st = three_term_step<float>(s, dt, static_cast<const float *>(v), static_cast<const float *>(vprev),
                                     static_cast<float *>(w), beta_prev, alpha, beta, true, e0, e1);
@@ -515,7 +710,7 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
 
 hb_status lanczos_workspace_bytes(hb_handle h, const hb_lanczos_opts *o, uint64_t *bytes) {
     if (!h || !o || !bytes || o->maxit < 1) return HB_ERR_INVALID_ARG;
-    if (o->vec_dtype != HB_F64 && o->vec_dtype != HB_F32) return HB_ERR_INVALID_ARG;
+    if (o->vec_dtype != HB_F64 && o->vec_dtype != HB_F32 && o->vec_dtype != HB_FX64) return HB_ERR_INVALID_ARG;
     *bytes = make_layout(h, *o).total;
     return HB_OK;
 }
@@ -525,7 +720,9 @@ hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *o, const void
                                hb_lanczos_info *info, void *stream) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!h || !o || !E0 || !workspace || o->maxit < 1 || o->check_every < 1) return HB_ERR_INVALID_ARG;
-    if (o->vec_dtype != HB_F64 && o->vec_dtype != HB_F32) return HB_ERR_INVALID_ARG;
+    if (o->vec_dtype != HB_F64 && o->vec_dtype != HB_F32 && o->vec_dtype != HB_FX64) return HB_ERR_INVALID_ARG;
+    if ((o->vec_dtype == HB_FX64 || o->fp64_finish == 2) && (!h->fx_ok || o->reorth)) return HB_ERR_INVALID_ARG;
+    if (o->fp64_finish < 0 || o->fp64_finish > 2) return HB_ERR_INVALID_ARG;
     const Layout L = make_layout(h, *o);
     if (workspace_bytes < L.total) return HB_ERR_NO_MEMORY;
     if ((uintptr_t)workspace % 256 != 0) return HB_ERR_INVALID_ARG;
@@ -546,7 +743,7 @@ hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *o, const void
     s.grid_vec = h->sm_count * 8;
     const uint64_t D = h->D;
     const hb_dtype dt = (hb_dtype)o->vec_dtype;
-    const uint64_t es = dt == HB_F64 ? 8 : 4;
+    const uint64_t es = dt == HB_F32 ? 4 : 8;
     const uint64_t stride = align256(D * es) / es;
     const bool reorth = o->reorth != 0;
     const double tol = o->tol;
@@ -562,6 +759,14 @@ hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *o, const void
             k_fill_random<double><<<s.grid_vec, kRedThreads, 0, s.st>>>(V, D, o->seed);
         if ((st = normalise(s, V)) != HB_OK) return st;
         st = lanczos_run<double>(s, HB_F64, V, stride, o->maxit, reorth, tol, o->check_every, r);
+    } else if (dt == HB_FX64) {
+        int64_t *V = reinterpret_cast<int64_t *>(ws + L.vec);
+        if (v0)
+            k_copy<int64_t><<<s.grid_vec, kRedThreads, 0, s.st>>>(static_cast<const int64_t *>(v0), V, D);
+        else
+            k_fill_random_fx<<<s.grid_vec, kRedThreads, 0, s.st>>>(V, D, o->seed, h->fx_frac);
+        if ((st = normalise(s, V)) != HB_OK) return st;
+        st = lanczos_run<int64_t>(s, HB_FX64, V, stride, o->maxit, false, tol, o->check_every, r);
     } else {
         float *V = reinterpret_cast<float *>(ws + L.vec);
         if (v0)
@@ -605,13 +810,20 @@ hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *o, const void
                 wbuf = old_vp;
             }
             PD_CUDA(cudaGetLastError());
-            double *V64 = reinterpret_cast<double *>(ws + L.vec2 + align256(D * 4));
             const uint64_t stride64 = align256(D * 8) / 8;
-            k_f32_to_f64<<<s.grid_vec, kRedThreads, 0, s.st>>>(y, V64, D);
-            if ((st = normalise(s, V64)) != HB_OK) return st;
             const int rest = std::max(1, o->maxit - m);
             ran_finish = true;
-            st = lanczos_run<double>(s, HB_F64, V64, stride64, rest, false, tol, o->check_every, r);
+            if (o->fp64_finish == 2) {
+                int64_t *Vfx = reinterpret_cast<int64_t *>(ws + L.vec2 + align256(D * 4));
+                k_f32_to_fx<<<s.grid_vec, kRedThreads, 0, s.st>>>(y, Vfx, D, h->fx_frac);
+                if ((st = normalise(s, Vfx)) != HB_OK) return st;
+                st = lanczos_run<int64_t>(s, HB_FX64, Vfx, stride64, rest, false, tol, o->check_every, r);
+            } else {
+                double *V64 = reinterpret_cast<double *>(ws + L.vec2 + align256(D * 4));
+                k_f32_to_f64<<<s.grid_vec, kRedThreads, 0, s.st>>>(y, V64, D);
+                if ((st = normalise(s, V64)) != HB_OK) return st;
+                st = lanczos_run<double>(s, HB_F64, V64, stride64, rest, false, tol, o->check_every, r);
+            }
         }
     }
     PD_CUDA(cudaStreamSynchronize(s.st));
@@ -675,7 +887,7 @@ extern "C" hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *
     if (dev != h->device || dev < 0 || dev >= PD_NOALLOC_MAX_DEVICES) return HB_ERR_INVALID_ARG;
     uint64_t need = 0;
     lanczos_step_scratch_bytes(h, &need);
-    const uint64_t nblk = need / sizeof(double);
+    const uint64_t nblk = need / 16;  // one float64 partial per block is used here
     if (nblk > PD_NOALLOC_PARTIALS) return HB_ERR_NO_MEMORY;  // device wider than the fixed scratch
     double *partials = nullptr;
     {

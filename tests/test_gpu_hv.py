@@ -150,3 +150,66 @@ def test_hv_square4x4_full_vector_vs_tensor_product_oracle(env, square4x4):
     y = pd.hubbard_apply(h, torch.from_numpy(x).cuda()).cpu().numpy()
     assert np.max(np.abs(y - yr)) <= 1e-12 * np.max(np.abs(yr))
     h.close()
+
+
+# ---------------------------------------------------------------- fixed point (HB_FX64)
+
+FX_CASES = [(wl.ring(8), 4, 4, 4.0), (wl.rect_periodic(4, 3), 5, 3, 7.5), (wl.rect_periodic(3, 3, 1.0, -0.3), 4, 5, 8.0),
+            (wl.ring(12), 6, 6, 3.0), (wl.ring(10), 0, 5, 2.0), (wl.dimer(), 1, 1, 4.0), (wl.tilted_18(), 2, 2, 6.0)]
+
+
+@pytest.mark.parametrize("cl,nu,nd,U", FX_CASES)
+def test_hv_fx64_matches_oracle(env, cl, nu, nd, U):
+    """Fixed-point H·v: exact integer hop sums, one rounding per amplitude class and for U docc."""
+    torch, pd = env
+    m = Model.from_cluster(cl, U, nu, nd)
+    b = Basis(cl.L, nu, nd)
+    h = handle_for(cl, U, nu, nd)
+    F = pd.hubbard_fixed_point_bits(h)
+    assert 20 <= F <= 60
+    x = start_vector(11, b.D)                      # |x| < 1
+    xt = torch.from_numpy(x).cuda()
+    q = pd.hubbard_convert(h, xt, torch.int64)
+    assert torch.equal(q.cpu(), torch.from_numpy(np.rint(np.ldexp(x, F)).astype(np.int64)))
+    xq = np.ldexp(q.cpu().numpy().astype(np.float64), -F)   # the input the fixed-point kernel sees
+    yq = pd.hubbard_apply(h, q)
+    y = pd.hubbard_convert(h, yq, torch.float64).cpu().numpy()
+    yr = apply(m, b, xq)
+    n_classes = len(set(cl.t))
+    err = np.abs(y - yr)
+    assert err.max() <= 1e-12 * max(np.abs(yr).max(), 1e-300)
+    assert np.all(err <= (n_classes + 2) * 2.0 ** -F + 64 * EPS64 * abs_bound(m, b, xq))
+    h.close()
+
+
+def test_hv_fx64_square4x4_full_size_sampled(env, square4x4):
+    torch, pd = env
+    cl, m, b = square4x4
+    h = handle_for(cl, 8.0, 8, 8)
+    F = pd.hubbard_fixed_point_bits(h)
+    x = start_vector(0, b.D)
+    q = pd.hubbard_convert(h, torch.from_numpy(x).cuda(), torch.int64)
+    yq = pd.hubbard_apply(h, q)
+    rng = np.random.default_rng(4)
+    rows = np.unique(np.concatenate([[0, 1, b.D - 1, 12869, 12870], rng.integers(0, b.D, 300)]))
+    idx = torch.from_numpy(rows).cuda()
+    ys = np.ldexp(yq[idx].cpu().numpy().astype(np.float64), -F)
+    xq_all = q.cpu().numpy()
+    for r, yv in zip(rows, ys):
+        c, v = row(m, b, int(r))
+        xc = np.ldexp(xq_all[c].astype(np.float64), -F)
+        ref = float(np.dot(v, xc))
+        assert abs(yv - ref) <= 4 * 2.0 ** -F + 64 * EPS64 * float(np.dot(np.abs(v), np.abs(xc))), (r, yv, ref)
+    h.close()
+
+
+def test_fx64_rejected_for_too_many_amplitudes(env):
+    torch, pd = env
+    cl = wl.ring(6)
+    h = pd.Handle(6, cl.bonds, [1.0, 1.1, 1.2, 1.3, 1.4, 1.5], 1.0, 3, 3)
+    q = torch.zeros(h.D, dtype=torch.int64, device="cuda")
+    with pytest.raises(pd.HubbardError):
+        pd.hubbard_apply(h, q)
+    # the float paths still work
+    pd.hubbard_apply(h, torch.zeros(h.D, dtype=torch.float64, device="cuda"))
+    h.close()

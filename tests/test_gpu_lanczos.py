@@ -140,3 +140,74 @@ def test_square4x4_mixed_precision_ground_state(env):
     r = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0, dtype=torch.float32, fp64_finish=True)
     assert r.converged and close(r.E0, rec["E0"])
     h.close()
+
+
+# ---------------------------------------------------------------- fixed point (HB_FX64)
+
+def test_ring8_fx64_to_tolerance(env):
+    torch, pd = env
+    h = handle_for(wl.ring(8), 4.0, 4, 4)
+    r = pd.lanczos_ground_state(h, maxit=400, tol=1e-10, dtype=torch.int64)
+    assert r.converged and close(r.E0, golden("ring8_U4_4_4")["E0"])
+    h.close()
+
+
+def test_ring8_mixed_fx64_finish(env):
+    torch, pd = env
+    h = handle_for(wl.ring(8), 4.0, 4, 4)
+    r = pd.lanczos_ground_state(h, maxit=400, tol=1e-10, dtype=torch.float32, fp64_finish="fx64")
+    assert r.converged and r.iterations_f32 > 0
+    assert close(r.E0, golden("ring8_U4_4_4")["E0"])
+    h.close()
+
+
+def test_fx64_step_tracks_f64_step(env):
+    """Same start vector: alpha, beta of the fixed-point and float64 recurrences agree to ~1e-13."""
+    torch, pd = env
+    cl = wl.rect_periodic(4, 3)
+    h = handle_for(cl, 5.0, 5, 4)
+    x = torch.from_numpy(start_vector(5, h.D)).cuda()
+    x /= x.norm()
+    q = pd.hubbard_convert(h, x, torch.int64)
+    dev = torch.device("cuda")
+    scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device=dev)
+
+    def run(v0, steps=8):
+        V = [v0.clone(), torch.empty_like(v0), torch.empty_like(v0)]
+        a = torch.zeros(steps, dtype=torch.float64, device=dev)
+        b = torch.zeros(steps, dtype=torch.float64, device=dev)
+        for j in range(steps):
+            vp = V[(j - 1) % 3] if j > 0 else None
+            bp = b[j - 1:j] if j > 0 else None
+            pd.lanczos_step(h, V[j % 3], vp, V[(j + 1) % 3], bp, a[j:j + 1], b[j:j + 1], scratch)
+        return a.cpu().numpy(), b.cpu().numpy()
+
+    a64, b64 = run(x)
+    afx, bfx = run(q)
+    assert np.allclose(afx, a64, rtol=0, atol=1e-12)
+    assert np.allclose(bfx, b64, rtol=0, atol=1e-12)
+    h.close()
+
+
+def test_batch_instances_fx64_sample(env):
+    torch, pd = env
+    recs = golden("batch64")
+    insts = wl.draw_batch_instances(64)
+    for k in (2, 9, 40):
+        inst, rec = insts[k], recs[k]
+        h = handle_for(inst.cluster, inst.U, inst.N_up, inst.N_dn)
+        r = pd.lanczos_ground_state(h, maxit=2000, tol=1e-10, seed=inst.seed, dtype=torch.int64)
+        assert close(r.E0, rec["E0"]), (k, r.E0, rec["E0"])
+        h.close()
+
+
+def test_square4x4_fx64_ground_state(env):
+    torch, pd = env
+    rec = golden("square4x4_tp-0.3_U8_8_8")
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    h = handle_for(cl, 8.0, 8, 8)
+    r = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0, dtype=torch.int64)
+    assert r.converged and close(r.E0, rec["E0"])
+    r2 = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0, dtype=torch.float32, fp64_finish="fx64")
+    assert r2.converged and close(r2.E0, rec["E0"])
+    h.close()

@@ -136,3 +136,15 @@ def test_apply_rows_matches_apply():
     x = start_vector(6, b.D)
     rows = np.array([0, 5, 777, b.D - 1])
     assert np.array_equal(apply_rows(m, b, x, rows), apply(m, b, x)[rows])
+
+
+@pytest.mark.parametrize("cl,nu,nd,U", [(wl.ring(8), 4, 4, 4.0), (wl.rect_periodic(3, 3, 1.0, -0.3), 4, 3, 2.0),
+                                        (wl.tilted_18(), 2, 3, 6.0)])
+def test_row_by_counting_matches_list_rows(cl, nu, nd, U):
+    from oracle.hamiltonian import row_by_counting
+    m = Model.from_cluster(cl, U, nu, nd)
+    b = Basis(cl.L, nu, nd)
+    for r in np.unique(np.linspace(0, b.D - 1, 37).astype(np.int64)):
+        c1, v1 = row(m, b, int(r))
+        c2, v2 = row_by_counting(m, int(r))
+        assert np.array_equal(c1, c2) and np.array_equal(v1, v2)
