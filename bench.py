@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "fx64", "f32"],
                    help="Krylov vector type: float64 (float64 FMAs), fixed-point int64, float32")
     p.add_argument("--no-solve", action="store_true", help="skip the time-to-E0 runs")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="keep the library's default H·v launch configuration")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return p.parse_args()
 
@@ -177,6 +179,7 @@ def run_ours(args, world, rank, local):
     beta = torch.zeros(nsteps + 1, dtype=torch.float64, device=dev)
     scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device=dev)
     pd.hubbard_apply(h, V[0], V[1])  # builds the per-spin tables (setup, untimed)
+    tuned = pd.hubbard_autotune(h, V[0], V[1], reps=2) if args.autotune else pd.hubbard_get_hv_config(h, vdt)
     torch.cuda.synchronize()
 
     launches = ctypes.c_uint32(0)
@@ -271,6 +274,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded random start vector)",
         "config": {**WORKLOADS[args.workload], **COMMON, "vector_dtype": args.dtype},
         "hv_ms": round(hv_ms, 4), "hv_gstates_per_s": round(D / (hv_ms * 1e-3) / 1e9, 4),
+        "hv_config": tuned,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "kernel": kname, "bytes_per_state": bps,

@@ -120,6 +120,26 @@ hb_status paradeisos_unrank(hb_handle h, const uint64_t *idx, uint64_t *states, 
  */
 hb_status hubbard_apply(hb_handle h, hb_dtype dt, const void *x, void *y, void *stream);
 
+/* Launch configuration of the H·v kernel for one vector type (zeros = library default). */
+typedef struct {
+    int32_t rows_per_cta;     /* rows of x staged together in shared memory: 1, 2 or 4 (0 = widest that fits) */
+    int32_t threads_per_cta;  /* multiple of 32, <= 1024 (0 = 1024) */
+    int32_t visit_order;      /* 1: rows in reverse Cuthill-McKee order of the spin-up hop graph (default);
+                                 0: storage order.  Only the visiting order changes, never the layout. */
+    float ms;                 /* hubbard_autotune: time per H·v of the chosen configuration */
+} hb_hv_config;
+
+hb_status hubbard_get_hv_config(hb_handle h, hb_dtype dt, hb_hv_config *cfg);
+/* HB_ERR_INVALID_ARG for out-of-range fields; a row count that does not fit
+ * shared memory falls back to the widest that does. */
+hb_status hubbard_set_hv_config(hb_handle h, hb_dtype dt, const hb_hv_config *cfg);
+/* Autotuner: times every candidate configuration (rows 1/2/4, threads
+ * 256/512/1024, both visiting orders) as reps applications of H to the caller's
+ * x (into y, which is overwritten), keeps the fastest in the handle and
+ * returns it in *best (may be NULL).  Synchronises `stream`. */
+hb_status hubbard_autotune(hb_handle h, hb_dtype dt, const void *x, void *y, int32_t reps, hb_hv_config *best,
+                           void *stream);
+
 /*
  * Verification export of matrix rows row0 .. row0+nrows-1 in canonical form:
  * entries sorted by column, the diagonal included even when it is zero.
@@ -232,6 +252,39 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
 hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w,
                                const double *beta_prev, double *alpha, double *beta, void *ev_hv_begin,
                                void *ev_hv_end, uint32_t *launches, void *stream);
+
+/* ---------------- batches of independent problems ---------------- */
+/*
+ * A batch groups handles (different clusters, sectors, U) that are applied and
+ * solved together: their vectors are concatenated, instance k occupying
+ * elements [offsets[k], offsets[k] + D_k) of a batch vector of offsets[n]
+ * elements (offsets are multiples of 64 elements).  The handles must outlive
+ * the batch and stay on one device; a batch is not a copy of their tables.
+ * (Not in the paper: a throughput arrangement for many small problems.)
+ */
+typedef struct hb_batch *hb_batch_handle;
+hb_status hubbard_batch_create(int n, const hb_handle *handles, hb_batch_handle *out);
+hb_status hubbard_batch_destroy(hb_batch_handle b);
+hb_status hubbard_batch_layout(hb_batch_handle b, uint64_t *offsets /* [n+1] */);
+/* y = H_k x for every instance k in one launch (row groups of all instances
+ * form one work list); dt HB_F64, HB_F32 or HB_FX64. */
+hb_status hubbard_batch_apply(hb_batch_handle b, hb_dtype dt, const void *x, void *y, void *stream);
+/* Autotuner of the batched H·v (rows per group 1/2/4, threads 128/256/512);
+ * keeps the fastest in the batch.  x and y are batch vectors (y overwritten). */
+hb_status hubbard_batch_autotune(hb_batch_handle b, hb_dtype dt, const void *x, void *y, int32_t reps,
+                                 hb_hv_config *best, void *stream);
+hb_status lanczos_batch_workspace_bytes(hb_batch_handle b, const hb_lanczos_opts *opts, uint64_t *bytes);
+/*
+ * Lowest eigenvalue of every instance by the three-term Lanczos recurrence
+ * (vec_dtype HB_F64 or HB_FX64; reorth and fp64_finish are not supported).
+ * Instance k starts from the SplitMix64 vector of seed opts->seed + k.  One
+ * step of all instances is captured once into a CUDA graph (per slot phase)
+ * and replayed; every check_every steps the host solves each instance's
+ * tridiagonal, and converged instances are masked out of later steps.
+ * E0, info: HOST arrays [n].  Synchronises `stream`.
+ */
+hb_status lanczos_batch_ground_state(hb_batch_handle b, const hb_lanczos_opts *opts, void *workspace,
+                                     uint64_t workspace_bytes, double *E0, hb_lanczos_info *info, void *stream);
 
 /*
  * Host utility (no GPU needed): lowest eigenvalue theta of the symmetric

@@ -31,6 +31,15 @@ class HubbardError(RuntimeError):
         super().__init__(f"{where}: {self.name}")
 
 
+class HvConfig(ctypes.Structure):
+    _fields_ = [("rows_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("visit_order", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"rows_per_cta": self.rows_per_cta, "threads_per_cta": self.threads_per_cta,
+                "visit_order": self.visit_order, "ms": self.ms}
+
+
 class LanczosOpts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int32), ("reorth", ctypes.c_int32), ("vec_dtype", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
@@ -68,6 +77,16 @@ def load():
                                                 ctypes.POINTER(D), ctypes.POINTER(LanczosInfo), P]),
         "hb_tridiag_lowest": (ctypes.c_int, [P, P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "hubbard_fixed_point_bits": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "hubbard_batch_create": (ctypes.c_int, [I32, P, ctypes.POINTER(P)]),
+        "hubbard_batch_destroy": (ctypes.c_int, [P]),
+        "hubbard_batch_layout": (ctypes.c_int, [P, P]),
+        "hubbard_batch_apply": (ctypes.c_int, [P, I32, P, P, P]),
+        "hubbard_batch_autotune": (ctypes.c_int, [P, I32, P, P, I32, ctypes.POINTER(HvConfig), P]),
+        "lanczos_batch_workspace_bytes": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), ctypes.POINTER(U64)]),
+        "lanczos_batch_ground_state": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, U64, P, P, P]),
+        "hubbard_get_hv_config": (ctypes.c_int, [P, I32, ctypes.POINTER(HvConfig)]),
+        "hubbard_set_hv_config": (ctypes.c_int, [P, I32, ctypes.POINTER(HvConfig)]),
+        "hubbard_autotune": (ctypes.c_int, [P, I32, P, P, I32, ctypes.POINTER(HvConfig), P]),
         "hubbard_convert": (ctypes.c_int, [P, I32, P, I32, P, U64, P]),
         "lanczos_step_scratch_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
         "lanczos_step": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, U64, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
@@ -202,6 +221,32 @@ def hubbard_fixed_point_bits(h: "Handle") -> int:
     return F.value
 
 
+def hubbard_get_hv_config(h: "Handle", dtype) -> dict:
+    c = HvConfig()
+    _check(load().hubbard_get_hv_config(h.ptr, _dtype_of(dtype), ctypes.byref(c)), "hubbard_get_hv_config")
+    return c.as_dict()
+
+
+def hubbard_set_hv_config(h: "Handle", dtype, rows_per_cta=0, threads_per_cta=0, visit_order=1):
+    c = HvConfig(int(rows_per_cta), int(threads_per_cta), int(visit_order), 0.0)
+    _check(load().hubbard_set_hv_config(h.ptr, _dtype_of(dtype), ctypes.byref(c)), "hubbard_set_hv_config")
+
+
+def hubbard_autotune(h: "Handle", x, y, reps: int = 3, stream=None) -> dict:
+    """Time every H·v launch configuration on x -> y, keep the fastest; returns it (with ms)."""
+    _need_cuda(x, y)
+    c = HvConfig()
+    _check(load().hubbard_autotune(h.ptr, _dtype_code(x), _ptr(x), _ptr(y), int(reps), ctypes.byref(c),
+                                   _stream_ptr(stream)), "hubbard_autotune")
+    return c.as_dict()
+
+
+def _dtype_of(dtype) -> int:
+    import torch
+    return {torch.float64: HB_F64, torch.float32: HB_F32, torch.int64: HB_FX64}[dtype] \
+        if not isinstance(dtype, int) else dtype
+
+
 def hubbard_convert(h: "Handle", x, out_dtype, stream=None):
     """float64 <-> fixed-point (int64) conversion of a device vector."""
     import torch
@@ -333,3 +378,79 @@ def hb_tridiag_lowest(alpha, beta):
     _check(load().hb_tridiag_lowest(ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(b.ctypes.data), len(a),
                                     ctypes.byref(th), ctypes.byref(sl)), "hb_tridiag_lowest")
     return th.value, sl.value
+
+
+class Batch:
+    """Owns an hb_batch_handle over a list of Handles (which must outlive it)."""
+
+    def __init__(self, handles):
+        import numpy as np
+        lib = load()
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.ptr.value for h in self.handles])
+        b = ctypes.c_void_p()
+        _check(lib.hubbard_batch_create(len(self.handles), arr, ctypes.byref(b)), "hubbard_batch_create")
+        self._b = b
+        off = np.zeros(len(self.handles) + 1, dtype=np.uint64)
+        _check(lib.hubbard_batch_layout(b, ctypes.c_void_p(off.ctypes.data)), "hubbard_batch_layout")
+        self.offsets = off.astype(np.int64)
+        self.total = int(off[-1])
+
+    def close(self):
+        if getattr(self, "_b", None) is not None:
+            load().hubbard_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def view(self, vec, k):
+        """Instance k's part of a batch vector."""
+        return vec[int(self.offsets[k]):int(self.offsets[k]) + self.handles[k].D]
+
+
+def hubbard_batch_apply(b: Batch, x, y=None, stream=None):
+    import torch
+    _need_cuda(x)
+    if x.numel() != b.total:
+        raise ValueError("x must have the batch length")
+    if y is None:
+        y = torch.zeros_like(x)
+    _check(load().hubbard_batch_apply(b._b, _dtype_code(x), _ptr(x), _ptr(y), _stream_ptr(stream)),
+           "hubbard_batch_apply")
+    return y
+
+
+def hubbard_batch_autotune(b: Batch, x, y, reps: int = 3, stream=None) -> dict:
+    _need_cuda(x, y)
+    c = HvConfig()
+    _check(load().hubbard_batch_autotune(b._b, _dtype_code(x), _ptr(x), _ptr(y), int(reps), ctypes.byref(c),
+                                         _stream_ptr(stream)), "hubbard_batch_autotune")
+    return c.as_dict()
+
+
+def lanczos_batch_ground_state(b: Batch, maxit: int = 1000, tol: float = 1e-10, dtype=None, seed: int = 0,
+                               check_every: int = 10, workspace=None, stream=None):
+    """Lowest eigenvalue of every instance; returns (E0 list, list of LanczosInfo dicts, status name)."""
+    import numpy as np
+    import torch
+    dt = {None: HB_F64, torch.float64: HB_F64, torch.int64: HB_FX64}[dtype]
+    o = LanczosOpts(int(maxit), 0, dt, int(check_every), float(tol), int(seed) & ((1 << 64) - 1), 0, 0)
+    lib = load()
+    nb = ctypes.c_uint64()
+    _check(lib.lanczos_batch_workspace_bytes(b._b, ctypes.byref(o), ctypes.byref(nb)), "lanczos_batch_workspace_bytes")
+    if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
+        workspace = torch.empty((nb.value,), dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+    n = len(b.handles)
+    E0 = np.zeros(n)
+    infos = (LanczosInfo * n)()
+    st = lib.lanczos_batch_ground_state(b._b, ctypes.byref(o), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(),
+                                        ctypes.c_void_p(E0.ctypes.data), infos, _stream_ptr(stream))
+    if st not in (0, 7):
+        raise HubbardError(st, "lanczos_batch_ground_state")
+    return E0.tolist(), [{"E0": i.E0, "residual": i.residual, "iterations": i.iterations,
+                          "converged": bool(i.converged), "seconds": i.seconds} for i in infos], STATUS[st]

@@ -48,6 +48,14 @@ struct FxCoef {
     int G = 1;
 };
 
+// Launch configuration of the H·v kernels (per vector type), set by
+// hubbard_set_hv_config or hubbard_autotune; zeros mean "library default".
+struct HvConfig {
+    int rows = 0;     // rows of x staged per CTA group (1, 2 or 4)
+    int threads = 0;  // threads per CTA (multiple of 32, <= 1024)
+    int order = 1;    // 1: reverse Cuthill-McKee row visiting order, 0: storage order
+};
+
 struct hb_basis {
     int L = 0, N_up = 0, N_dn = 0, n_bonds = 0;
     double U = 0.0;
@@ -65,6 +73,7 @@ struct hb_basis {
     // Cuthill-McKee over the spin-up hop graph, so that rows processed close in
     // time share hop neighbours and their x rows are still in L2
     uint32_t *d_row_order = nullptr;  // [D_up]
+    HvConfig hv_cfg[3];               // indexed by hb_dtype
     int32_t *h_bonds = nullptr;
     double *h_t = nullptr;
     // fixed-point (HB_FX64) support

@@ -1,0 +1,46 @@
+"""H·v launch configurations: every configuration computes bit-identical results, and the
+autotuner keeps the fastest one."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle.lanczos import start_vector
+from tests.gpu_util import handle_for, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype_name", ["float64", "float32", "int64"])
+def test_all_configs_bit_identical(dtype_name):
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    dtype = getattr(torch, dtype_name)
+    h = handle_for(wl.rect_periodic(3, 3, 1.0, -0.3), 5.0, 4, 4)
+    x = torch.from_numpy(start_vector(3, h.D)).cuda()
+    x = pd.hubbard_convert(h, x / x.abs().max(), torch.int64) if dtype_name == "int64" else x.to(dtype)
+    ref = pd.hubbard_apply(h, x).cpu()
+    for rows in (1, 2, 4):
+        for threads in (64, 256, 512, 1024):
+            for order in (0, 1):
+                pd.hubbard_set_hv_config(h, dtype, rows, threads, order)
+                y = pd.hubbard_apply(h, x).cpu()
+                assert torch.equal(y, ref), (rows, threads, order)
+    h.close()
+
+
+def test_autotune_keeps_fastest_and_results_unchanged():
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    h = handle_for(wl.ring(12), 3.0, 6, 6)
+    x = torch.from_numpy(start_vector(4, h.D)).cuda()
+    ref = pd.hubbard_apply(h, x).clone()
+    y = torch.empty_like(x)
+    best = pd.hubbard_autotune(h, x, y, reps=2)
+    assert best["ms"] > 0 and best["rows_per_cta"] in (1, 2, 4) and best["threads_per_cta"] in (256, 512, 1024)
+    cur = pd.hubbard_get_hv_config(h, torch.float64)
+    assert (cur["rows_per_cta"], cur["threads_per_cta"], cur["visit_order"]) == \
+        (best["rows_per_cta"], best["threads_per_cta"], best["visit_order"])
+    assert torch.equal(pd.hubbard_apply(h, x), ref)
+    with pytest.raises(pd.HubbardError):
+        pd.hubbard_set_hv_config(h, torch.float64, 3, 100, 0)
+    h.close()
