@@ -21,6 +21,8 @@
         if (e_ != cudaSuccess) return HB_ERR_CUDA;      \
     } while (0)
 
+#define PD_TGT_MASK 0x7FFFFFFFu  // target bits of a fixed-point hop entry (bit 31: sign)
+
 // Per-spin tables of one sector: the ascending list of strings (built by the
 // backward map) and the hop lists in ELL layout, entry k of string r at
 // [k * D + r], so that threads handling consecutive strings read consecutive
@@ -35,9 +37,9 @@ struct SpinTables {
     uint32_t *target = nullptr;  // [zmax * D]
     double *val = nullptr;       // [zmax * D]
     float *valf = nullptr;       // [zmax * D] binary32 copy of val
-    // fixed-point path: the same hops re-ordered by (amplitude class, sign),
-    // ftarget[k * D + r]; seg[r] packs the 2*PD_FX_MAXC segment lengths as bytes
-    // (class c, sign +) at byte 2c and (class c, sign -) at byte 2c+1.
+    // fixed-point path: the same hops grouped by amplitude class,
+    // ftarget[k * D + r] = target | (negative sign << 31); seg[r] packs the
+    // per-class counts as bytes (class c at byte c).
     uint32_t *ftarget = nullptr;
     uint64_t *seg = nullptr;
 };

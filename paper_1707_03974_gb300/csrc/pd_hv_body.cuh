@@ -87,22 +87,40 @@ __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict
             const T xv = SMEM ? s_x[d * R + r] : (r < nr ? x[ur[r] * Dd + d] : T(0));
             acc[r] = a.U * (T)__popc(su[r] & sd) * xv;
         }
-        // spin-down hops: gather within the staged rows
+        // spin-down hops: gather within the staged rows (table loads issued in batches of 4)
         const int nd = a.cnt_dn[d];
-        for (int k = 0; k < nd; ++k) {
-            const uint64_t dk = a.tgt_dn[(uint64_t)k * Dd + d];
-            const T v = a.val_dn[(uint64_t)k * Dd + d];
+        for (int k0 = 0; k0 < nd; k0 += 4) {
+            uint32_t tk[4];
+            T vk[4];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const T xv = SMEM ? s_x[dk * R + r] : (r < nr ? x[ur[r] * Dd + dk] : T(0));
-                acc[r] += v * xv;
-            }
+            for (int i = 0; i < 4; ++i)
+                if (k0 + i < nd) {
+                    tk[i] = a.tgt_dn[(uint64_t)(k0 + i) * Dd + d];
+                    vk[i] = a.val_dn[(uint64_t)(k0 + i) * Dd + d];
+                }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (k0 + i < nd) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const T xv = SMEM ? s_x[(uint64_t)tk[i] * R + r] : (r < nr ? x[ur[r] * Dd + tk[i]] : T(0));
+                        acc[r] += vk[i] * xv;
+                    }
+                }
         }
-        // spin-up hops: rows x[u', :] read at column d (coalesced across the CTA)
+        // spin-up hops: rows x[u', :] read at column d (coalesced across the CTA), 8 loads in flight
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int nu = s_nup[r];
-            for (int k = 0; k < nu; ++k) acc[r] += s_uval[r * zr + k] * x[(uint64_t)s_ucol[r * zr + k] * Dd + d];
+            for (int k0 = 0; k0 < nu; k0 += 8) {
+                T xv[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    xv[i] = (k0 + i < nu) ? x[(uint64_t)s_ucol[r * zr + k0 + i] * Dd + d] : T(0);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (k0 + i < nu) acc[r] += s_uval[r * zr + k0 + i] * xv[i];
+            }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -111,11 +129,12 @@ __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// Fixed-point (HB_FX64) group.  Hops are grouped per spin string into segments
-// of equal amplitude class c and fermion sign; the group adds the raw 64-bit
-// integers of each segment (exact), then applies each class's amplitude -t_c
-// once per element: y = U docc x + sum_c (-t_c) (P_c - N_c), each product
-// rounded once.  The float64 pipe is never used.
+// Fixed-point (HB_FX64) group.  Hops are grouped per spin string by amplitude
+// class c, each carrying its fermion sign; the group forms the exact integer
+// sums S_c = sum sigma_k x_k (a negative term added as (x XOR -1) + 1), then
+// applies each class's amplitude -t_c once per element:
+//     y = U docc x + sum_c (-t_c) S_c,
+// each product rounded once.  The float64 pipe is never used.
 struct FxArgs {
     uint64_t Du, Dd;
     const uint32_t *str_up, *str_dn;
@@ -192,32 +211,62 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
     for (int r = 0; r < R; ++r) su[r] = r < nr ? a.str_up[ur[r]] : 0u;
 
     for (uint64_t d = threadIdx.x; d < Dd; d += blockDim.x) {
-        int64_t acc[R][2 * NC];
+        int64_t acc[R][NC];
+        int negB[NC];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+        for (int c = 0; c < NC; ++c) {
+            negB[c] = 0;
 #pragma unroll
-            for (int q = 0; q < 2 * NC; ++q) acc[r][q] = 0;
-        // spin-down hops of column d: gathers within the staged rows
+            for (int r = 0; r < R; ++r) acc[r][c] = 0;
+        }
+        // spin-down hops of column d: gathers within the staged rows, table loads in batches of 4
         const uint64_t sg = a.seg_dn[d];
         uint64_t k = 0;
 #pragma unroll
-        for (int q = 0; q < 2 * NC; ++q) {
-            const int n = (int)((sg >> (8 * q)) & 0xFFu);
-            for (int i = 0; i < n; ++i, ++k) {
-                const uint64_t dk = a.ft_dn[k * Dd + d];
+        for (int c = 0; c < NC; ++c) {
+            const int n = (int)((sg >> (8 * c)) & 0xFFu);
+            for (int i0 = 0; i0 < n; i0 += 4) {
+                uint32_t e[4];
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r][q] += SMEM ? s_x[dk * R + r] : (r < nr ? x[ur[r] * Dd + dk] : 0);
+                for (int i = 0; i < 4; ++i)
+                    if (i0 + i < n) e[i] = a.ft_dn[(k + i0 + i) * Dd + d];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (i0 + i < n) {
+                        const int64_t m = (int64_t)((int32_t)e[i] >> 31);
+                        const uint64_t dk = e[i] & PD_TGT_MASK;
+                        negB[c] += (int)(e[i] >> 31);
+#pragma unroll
+                        for (int r = 0; r < R; ++r)
+                            acc[r][c] += (SMEM ? s_x[dk * R + r] : (r < nr ? x[ur[r] * Dd + dk] : 0)) ^ m;
+                    }
             }
+            k += n;
         }
-        // spin-up hops of row ur[r]: rows x[u', :] at column d
+        // spin-up hops of row ur[r] (the same list for the whole CTA): 8 loads in flight
+        int negA[R][NC];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint64_t ug = s_useg[r];
             int kk = 0;
 #pragma unroll
-            for (int q = 0; q < 2 * NC; ++q) {
-                const int n = (int)((ug >> (8 * q)) & 0xFFu);
-                for (int i = 0; i < n; ++i, ++kk) acc[r][q] += x[(uint64_t)s_ucol[r * zr + kk] * Dd + d];
+            for (int c = 0; c < NC; ++c) {
+                negA[r][c] = 0;
+                const int n = (int)((ug >> (8 * c)) & 0xFFu);
+                for (int i0 = 0; i0 < n; i0 += 8) {
+                    int64_t xv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        xv[i] = (i0 + i < n) ? x[(uint64_t)(s_ucol[r * zr + kk + i0 + i] & PD_TGT_MASK) * Dd + d] : 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i0 + i < n) {
+                            const uint32_t e = s_ucol[r * zr + kk + i0 + i];
+                            acc[r][c] += xv[i] ^ (int64_t)((int32_t)e >> 31);
+                            negA[r][c] += (int)(e >> 31);
+                        }
+                }
+                kk += n;
             }
         }
         const uint32_t sd = a.str_dn[d];
@@ -228,7 +277,7 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
             const int64_t xd = SMEM ? s_x[d * R + r] : x[ur[r] * Dd + d];
             int64_t out = fx_mul(xd, s_kd[docc], s_gd[docc]);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) out += fx_mul(acc[r][2 * c] - acc[r][2 * c + 1], a.Kc[c], a.Gc[c]);
+            for (int c = 0; c < NC; ++c) out += fx_mul(acc[r][c] + negB[c] + negA[r][c], a.Kc[c], a.Gc[c]);
             y[ur[r] * Dd + d] = out;
         }
     }
