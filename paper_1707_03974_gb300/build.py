@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUTDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUTDIR, "libparadeisos.so")
-SOURCES = ["pd_basis.cu", "pd_hv.cu", "pd_lanczos.cu", "pd_batch.cu"]
+SOURCES = ["pd_basis.cu", "pd_hv.cu", "pd_lanczos.cu", "pd_batch.cu", "pd_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
@@ -34,7 +34,7 @@ def _stale(lib: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "pd_common.cuh"), os.path.join(CSRC, "pd_hv_body.cuh"),
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "pd_common.cuh"), os.path.join(CSRC, "pd_hv_body.cuh"), os.path.join(CSRC, "pd_tc.cuh"), os.path.join(ROOT, "include", "paradeisos_mlp.h"),
                                                        os.path.join(ROOT, "include", "paradeisos.h")]
     if not force and not _stale(LIB, deps):
         return LIB

@@ -1,0 +1,586 @@
+// Learned Lanczos start vector: a small multilayer perceptron over the 2L
+// occupation bits of a basis state (not part of the paper; an addition that
+// re-uses the method's own ground states as training data).
+//
+//   z1 = W1 x + b1, a1 = gelu(z1), z2 = W2 a1 + b2, a2 = gelu(z2), out = W3 a2 + b3
+//   out = (log|psi|, sign logit),  hidden width 128, gelu in the exact erf form.
+//
+// Weights are kept in float32 (master copy, Adam) and used as bfloat16; the two
+// 128-wide matrix products of the forward pass, and the activation-gradient and
+// weight-gradient products of the backward pass, run on the tensor cores
+// through tcgen05.mma (bf16 x bf16 -> f32 in tensor memory, pd_tc.cuh).  The
+// 2-wide output layer and the element-wise parts run on the CUDA cores.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "pd_common.cuh"
+#include "pd_tc.cuh"
+#include "paradeisos_mlp.h"
+
+namespace {
+
+constexpr int kH = 128;    // hidden width
+constexpr int kIn = 32;    // padded input width (2L <= 32)
+constexpr int kBM = 128;   // GEMM tile rows (MMA M)
+constexpr int kBK = 64;    // GEMM K chunk
+constexpr uint32_t kWaitTries = 1u << 24;
+
+// ---------------------------------------------------------------------------
+// Generic tcgen05 GEMM:  C[M, N] (+)= A[M, K] * B[N, K]^T  (A, B bf16 row-major,
+// K contiguous; C f32 row-major).  One CTA of 128 threads per 128 x BN tile and
+// K range; the tiles are copied to shared memory in the core-matrix layout, one
+// thread issues the MMAs, the accumulator lives in tensor memory and the four
+// warps read it back (warp w owns rows 32w .. 32w+31).  mode 0: C = acc,
+// mode 1: atomicAdd(C, acc) (split K / accumulation).  Columns >= n_store are
+// not written.
+template <int BN>
+__global__ void __launch_bounds__(128) k_tc_gemm(const __nv_bfloat16 *__restrict__ A, int lda,
+                                                 const __nv_bfloat16 *__restrict__ B, int ldb, float *C, int ldc,
+                                                 int M, int N, int K, int k_per_cta, int n_store, int mode,
+                                                 unsigned *err) {
+    __shared__ __align__(1024) uint8_t sA[kBM * kBK * 2];
+    __shared__ __align__(1024) uint8_t sB[BN * kBK * 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    constexpr uint32_t kCols = BN < 32 ? 32 : BN;
+    constexpr uint32_t kSBO = (kBK / 8) * 128;  // bytes between 8-row groups
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kCols);
+    if (tid == 0) tc::mbar_init(&bar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * k_per_cta, ke = min(K, kb + k_per_cta);
+    constexpr uint32_t idesc = tc::make_idesc_bf16(kBM, BN);
+    uint32_t phase = 0;
+    bool ok = true, any = false;
+    for (int k0 = kb; k0 < ke && ok; k0 += kBK) {
+        // 16-byte chunks: row r, K-group kc (8 elements)
+        for (int c = tid; c < kBM * (kBK / 8); c += 128) {
+            const int r = c / (kBK / 8), kc = c % (kBK / 8);
+            const int gk = k0 + kc * 8, gr = m0 + r;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (gr < M && gk + 8 <= ke) v = *reinterpret_cast<const uint4 *>(A + (size_t)gr * lda + gk);
+            *reinterpret_cast<uint4 *>(sA + tc::core_off(r, kc * 8, kSBO)) = v;
+        }
+        for (int c = tid; c < BN * (kBK / 8); c += 128) {
+            const int r = c / (kBK / 8), kc = c % (kBK / 8);
+            const int gk = k0 + kc * 8, gr = n0 + r;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (gr < N && gk + 8 <= ke) v = *reinterpret_cast<const uint4 *>(B + (size_t)gr * ldb + gk);
+            *reinterpret_cast<uint4 *>(sB + tc::core_off(r, kc * 8, kSBO)) = v;
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+            for (int ks = 0; ks < kBK / 16; ++ks) {
+                const uint64_t ad = tc::make_desc(a0 + ks * 256, 128, kSBO);
+                const uint64_t bd = tc::make_desc(b0 + ks * 256, 128, kSBO);
+                tc::mma_bf16(tmem, ad, bd, idesc, (any || ks > 0) ? 1u : 0u);
+            }
+            tc::commit(&bar);
+        }
+        ok = tc::mbar_wait(&bar, phase, kWaitTries);
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;  // uniform decision for the whole CTA
+        phase ^= 1;
+        any = true;
+        tc::fence_after_sync();
+    }
+    if (!ok && tid == 0) atomicOr(err, PD_ERRBIT(HB_ERR_TIMEOUT));
+    if (ok && any) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row < M) {
+                float *crow = C + (size_t)row * ldc + n0 + c0;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int col = n0 + c0 + i;
+                    if (col < n_store) {
+                        if (mode == 0) crow[i] = v[i];
+                        else atomicAdd(crow + i, v[i]);
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+// ---------------------------------------------------------------------------
+// element-wise kernels
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+
+// x rows: bit i of the combined state -> column i (0/1), columns >= n_bits zero.
+__global__ void k_bits(const uint64_t *__restrict__ states, uint64_t n, uint64_t n_pad, int n_bits,
+                       __nv_bfloat16 *__restrict__ X) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n_pad * kIn; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = e / kIn;
+        const int i = (int)(e % kIn);
+        float v = 0.f;
+        if (r < n && i < n_bits) v = (float)((states[r] >> i) & 1ull);
+        X[e] = __float2bfloat16_rn(v);
+    }
+}
+
+// Combined states of basis indices idx0 .. idx0+n-1 from the per-spin tables (backward map).
+__global__ void k_states_of_range(const uint32_t *__restrict__ str_up, const uint32_t *__restrict__ str_dn,
+                                  uint64_t D_dn, int L, uint64_t idx0, uint64_t n, uint64_t *__restrict__ out) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t I = idx0 + e;
+        const uint64_t u = I / D_dn, d = I - u * D_dn;
+        out[e] = ((uint64_t)str_up[u] << L) | (uint64_t)str_dn[d];
+    }
+}
+
+// A1 = bf16(gelu(Z1 + b1))
+__global__ void k_bias_gelu_bf16(const float *__restrict__ Z, const float *__restrict__ b, uint64_t rows,
+                                 __nv_bfloat16 *__restrict__ Aout) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < rows * kH; e += (uint64_t)gridDim.x * blockDim.x)
+        Aout[e] = __float2bfloat16_rn(gelu_f(Z[e] + b[e % kH]));
+}
+
+// out[r] = W3 gelu(Z2[r] + b2) + b3  (W3 used at bfloat16 precision)
+__global__ void k_output(const float *__restrict__ Z2, const float *__restrict__ b2, const float *__restrict__ W3,
+                         const float *__restrict__ b3, uint64_t n, float *__restrict__ out) {
+    __shared__ float s_w3[2 * kH], s_b2[kH];
+    for (int i = threadIdx.x; i < 2 * kH; i += blockDim.x) s_w3[i] = __bfloat162float(__float2bfloat16_rn(W3[i]));
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) s_b2[i] = b2[i];
+    __syncthreads();
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+        const float *z = Z2 + r * kH;
+        float o0 = b3[0], o1 = b3[1];
+        for (int h = 0; h < kH; ++h) {
+            const float a = gelu_f(z[h] + s_b2[h]);
+            o0 = fmaf(s_w3[h], a, o0);
+            o1 = fmaf(s_w3[kH + h], a, o1);
+        }
+        out[2 * r] = o0;
+        out[2 * r + 1] = o1;
+    }
+}
+
+// Backward through the output layer.  wts are the normalised sample weights.
+// Writes dZ2 (bf16, rows x 128) and its transpose (128 x n_pad), accumulates
+// gW3, gb3, gb2 and the loss into grad / loss.
+__global__ void k_output_back(const float *__restrict__ Z2, const float *__restrict__ b2, const float *__restrict__ W3,
+                              const float *__restrict__ out, const float *__restrict__ t_log,
+                              const float *__restrict__ t_sign, const float *__restrict__ wts, float lam, uint64_t n,
+                              uint64_t n_pad, __nv_bfloat16 *__restrict__ dZ2, __nv_bfloat16 *__restrict__ dZ2T,
+                              float *__restrict__ gW3, float *__restrict__ gb3, float *__restrict__ gb2,
+                              float *__restrict__ loss) {
+    __shared__ float s_w3[2 * kH], s_b2[kH], s_g[3 * kH + 2];
+    for (int i = threadIdx.x; i < 2 * kH; i += blockDim.x) s_w3[i] = __bfloat162float(__float2bfloat16_rn(W3[i]));
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) s_b2[i] = b2[i];
+    for (int i = threadIdx.x; i < 3 * kH + 2; i += blockDim.x) s_g[i] = 0.f;
+    __syncthreads();
+    float my_loss = 0.f;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n_pad; r += (uint64_t)gridDim.x * blockDim.x) {
+        if (r >= n) {
+            for (int h = 0; h < kH; ++h) {
+                dZ2[r * kH + h] = __float2bfloat16_rn(0.f);
+                dZ2T[(uint64_t)h * n_pad + r] = __float2bfloat16_rn(0.f);
+            }
+            continue;
+        }
+        const float w = wts[r];
+        const float e = out[2 * r] - t_log[r];
+        const float m = -t_sign[r] * out[2 * r + 1];
+        my_loss += w * (e * e + lam * (m > 20.f ? m : log1pf(__expf(m))));
+        const float d0 = w * 2.f * e;
+        const float d1 = w * lam * (-t_sign[r]) / (1.f + __expf(-m));
+        atomicAdd(&s_g[3 * kH], d0);
+        atomicAdd(&s_g[3 * kH + 1], d1);
+        for (int h = 0; h < kH; ++h) {
+            const float z = Z2[r * kH + h] + s_b2[h];
+            const float a = gelu_f(z);
+            atomicAdd(&s_g[h], d0 * a);
+            atomicAdd(&s_g[kH + h], d1 * a);
+            const float dz = (d0 * s_w3[h] + d1 * s_w3[kH + h]) * gelu_grad_f(z);
+            atomicAdd(&s_g[2 * kH + h], dz);
+            const __nv_bfloat16 bz = __float2bfloat16_rn(dz);
+            dZ2[r * kH + h] = bz;
+            dZ2T[(uint64_t)h * n_pad + r] = bz;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * kH; i += blockDim.x) atomicAdd(&gW3[i], s_g[i]);
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) atomicAdd(&gb2[i], s_g[2 * kH + i]);
+    if (threadIdx.x < 2) atomicAdd(&gb3[threadIdx.x], s_g[3 * kH + threadIdx.x]);
+    for (int o = 16; o > 0; o >>= 1) my_loss += __shfl_down_sync(0xffffffffu, my_loss, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, my_loss);
+}
+
+// dZ1 = dA1 * gelu'(Z1 + b1) -> transpose (128 x n_pad, bf16); gb1 += column sums.
+__global__ void k_hidden_back(const float *__restrict__ dA1, const float *__restrict__ Z1, const float *__restrict__ b1,
+                              uint64_t n, uint64_t n_pad, __nv_bfloat16 *__restrict__ dZ1T, float *__restrict__ gb1) {
+    __shared__ float s_g[kH];
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) s_g[i] = 0.f;
+    __syncthreads();
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n_pad * kH; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = e / kH;
+        const int h = (int)(e % kH);
+        float dz = 0.f;
+        if (r < n) {
+            dz = dA1[e] * gelu_grad_f(Z1[e] + b1[h]);
+            atomicAdd(&s_g[h], dz);
+        }
+        dZ1T[(uint64_t)h * n_pad + r] = __float2bfloat16_rn(dz);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) atomicAdd(&gb1[i], s_g[i]);
+}
+
+// (rows x cols) bf16 -> (cols x rows) bf16
+__global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ a, uint64_t rows, int cols,
+                                 __nv_bfloat16 *__restrict__ at) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < rows * cols; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = e / cols;
+        const int c = (int)(e % cols);
+        at[(uint64_t)c * rows + r] = a[e];
+    }
+}
+
+// master f32 parameters -> bf16 operands (W1 padded to 128 x 32, W2 and its transpose)
+__global__ void k_refresh_bf16(const float *__restrict__ W1, const float *__restrict__ W2, int n_in,
+                               __nv_bfloat16 *__restrict__ W1b, __nv_bfloat16 *__restrict__ W2b,
+                               __nv_bfloat16 *__restrict__ W2tb) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kH * kH; e += gridDim.x * blockDim.x) {
+        const int o = e / kH, i = e % kH;
+        const __nv_bfloat16 v = __float2bfloat16_rn(W2[e]);
+        W2b[e] = v;
+        W2tb[i * kH + o] = v;
+        if (e < kH * kIn) {
+            const int oo = e / kIn, ii = e % kIn;
+            W1b[e] = __float2bfloat16_rn(ii < n_in ? W1[oo * n_in + ii] : 0.f);
+        }
+    }
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       uint64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// start vector entries: v = sign * exp(min(out0, 20) - 20)
+template <typename T>
+__global__ void k_start_values(const float *__restrict__ out, uint64_t n, T *__restrict__ v, int F) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+        const float a = __expf(fminf(out[2 * r], 20.f) - 20.f);
+        const float s = out[2 * r + 1] >= 0.f ? a : -a;
+        if constexpr (sizeof(T) == 8 && !std::is_floating_point<T>::value)
+            v[r] = (T)__double2ll_rn(ldexp((double)s, F - 1));
+        else
+            v[r] = (T)s;
+    }
+}
+
+int grid_of(uint64_t n, int sms) { return (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8)); }
+
+}  // namespace
+
+struct hb_mlp {
+    int n_in = 32, device = 0, sm_count = 0;
+    uint64_t P = 0;
+    float *d_p = nullptr, *d_m = nullptr, *d_v = nullptr, *d_g = nullptr, *d_loss = nullptr;
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2tb = nullptr;
+    unsigned *d_err = nullptr;
+    // batch workspace
+    uint64_t cap = 0;
+    __nv_bfloat16 *X = nullptr, *XT = nullptr, *A1 = nullptr, *A1T = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
+                  *dZ1T = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *dA1 = nullptr, *out = nullptr;
+    uint64_t *states = nullptr;
+    int adam_t = 0;
+    // offsets of the parameter blocks (float32 master vector, oracle layout)
+    uint64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
+};
+
+namespace {
+
+void free_ws(hb_mlp *m) {
+    cudaFree(m->X); cudaFree(m->XT); cudaFree(m->A1); cudaFree(m->A1T); cudaFree(m->dZ2); cudaFree(m->dZ2T);
+    cudaFree(m->dZ1T); cudaFree(m->Z1); cudaFree(m->Z2); cudaFree(m->dA1); cudaFree(m->out); cudaFree(m->states);
+    m->X = m->XT = m->A1 = m->A1T = m->dZ2 = m->dZ2T = m->dZ1T = nullptr;
+    m->Z1 = m->Z2 = m->dA1 = m->out = nullptr;
+    m->states = nullptr;
+    m->cap = 0;
+}
+
+hb_status ensure_ws(hb_mlp *m, uint64_t n_pad) {
+    if (n_pad <= m->cap) return HB_OK;
+    free_ws(m);
+    const uint64_t b = n_pad;
+    bool ok = cudaMalloc(&m->X, b * kIn * 2) == cudaSuccess && cudaMalloc(&m->XT, b * kIn * 2) == cudaSuccess &&
+              cudaMalloc(&m->A1, b * kH * 2) == cudaSuccess && cudaMalloc(&m->A1T, b * kH * 2) == cudaSuccess &&
+              cudaMalloc(&m->dZ2, b * kH * 2) == cudaSuccess && cudaMalloc(&m->dZ2T, b * kH * 2) == cudaSuccess &&
+              cudaMalloc(&m->dZ1T, b * kH * 2) == cudaSuccess && cudaMalloc(&m->Z1, b * kH * 4) == cudaSuccess &&
+              cudaMalloc(&m->Z2, b * kH * 4) == cudaSuccess && cudaMalloc(&m->dA1, b * kH * 4) == cudaSuccess &&
+              cudaMalloc(&m->out, b * 2 * 4) == cudaSuccess && cudaMalloc(&m->states, b * 8) == cudaSuccess;
+    if (!ok) {
+        free_ws(m);
+        return HB_ERR_NO_MEMORY;
+    }
+    m->cap = n_pad;
+    return HB_OK;
+}
+
+// C = A B^T on the tensor cores; split K over `split` CTAs when mode == 1 (atomic accumulation).
+hb_status gemm(hb_mlp *m, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, float *C, int ldc, int M,
+               int N, int K, int n_store, int mode, int split, cudaStream_t st) {
+    const int kpc = ((K + split - 1) / split + kBK - 1) / kBK * kBK;
+    const int zs = (K + kpc - 1) / kpc;
+    if (N <= 32) {
+        dim3 g((M + kBM - 1) / kBM, (N + 31) / 32, zs);
+        k_tc_gemm<32><<<g, 128, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kpc, n_store, mode, m->d_err);
+    } else {
+        dim3 g((M + kBM - 1) / kBM, (N + 127) / 128, zs);
+        k_tc_gemm<128><<<g, 128, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kpc, n_store, mode, m->d_err);
+    }
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+// forward of n_pad rows whose inputs are already in m->X; writes Z1, A1, Z2, out
+hb_status forward_rows(hb_mlp *m, uint64_t n, uint64_t n_pad, cudaStream_t st) {
+    hb_status s = gemm(m, m->X, kIn, m->W1b, kIn, m->Z1, kH, (int)n_pad, kH, kIn, kH, 0, 1, st);
+    if (s != HB_OK) return s;
+    k_bias_gelu_bf16<<<grid_of(n_pad * kH, m->sm_count), 256, 0, st>>>(m->Z1, m->d_p + m->ob1, n_pad, m->A1);
+    if ((s = gemm(m, m->A1, kH, m->W2b, kH, m->Z2, kH, (int)n_pad, kH, kH, kH, 0, 1, st)) != HB_OK) return s;
+    k_output<<<grid_of(n, m->sm_count), 256, 0, st>>>(m->Z2, m->d_p + m->ob2, m->d_p + m->oW3, m->d_p + m->ob3, n,
+                                                      m->out);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+void refresh(hb_mlp *m, cudaStream_t st) {
+    k_refresh_bf16<<<64, 256, 0, st>>>(m->d_p + m->oW1, m->d_p + m->oW2, m->n_in, m->W1b, m->W2b, m->W2tb);
+}
+
+}  // namespace
+
+extern "C" {
+
+hb_status mlp_create(int n_in, uint64_t seed, hb_mlp_handle *out) {
+    if (!out || n_in < 1 || n_in > kIn) return HB_ERR_INVALID_ARG;
+    *out = nullptr;
+    hb_mlp *m = new (std::nothrow) hb_mlp();
+    if (!m) return HB_ERR_NO_MEMORY;
+    m->n_in = n_in;
+    m->oW1 = 0;
+    m->ob1 = m->oW1 + (uint64_t)kH * n_in;
+    m->oW2 = m->ob1 + kH;
+    m->ob2 = m->oW2 + (uint64_t)kH * kH;
+    m->oW3 = m->ob2 + kH;
+    m->ob3 = m->oW3 + 2 * kH;
+    m->P = m->ob3 + 2;
+    cudaGetDevice(&m->device);
+    cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
+    bool ok = cudaMalloc(&m->d_p, m->P * 4) == cudaSuccess && cudaMalloc(&m->d_m, m->P * 4) == cudaSuccess &&
+              cudaMalloc(&m->d_v, m->P * 4) == cudaSuccess && cudaMalloc(&m->d_g, m->P * 4) == cudaSuccess &&
+              cudaMalloc(&m->d_loss, 4) == cudaSuccess && cudaMalloc(&m->W1b, kH * kIn * 2) == cudaSuccess &&
+              cudaMalloc(&m->W2b, kH * kH * 2) == cudaSuccess && cudaMalloc(&m->W2tb, kH * kH * 2) == cudaSuccess &&
+              cudaMalloc(&m->d_err, sizeof(unsigned)) == cudaSuccess;
+    if (!ok) {
+        mlp_destroy(m);
+        return HB_ERR_NO_MEMORY;
+    }
+    // initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), zero biases
+    std::vector<float> p(m->P, 0.f);
+    uint64_t st = seed;
+    auto uni = [&]() {
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * 0x1.0p-52 - 1.0;
+    };
+    for (uint64_t i = 0; i < (uint64_t)kH * n_in; ++i) p[m->oW1 + i] = (float)(uni() / std::sqrt((double)n_in));
+    for (uint64_t i = 0; i < (uint64_t)kH * kH; ++i) p[m->oW2 + i] = (float)(uni() / std::sqrt((double)kH));
+    for (uint64_t i = 0; i < 2ull * kH; ++i) p[m->oW3 + i] = (float)(uni() / std::sqrt((double)kH));
+    cudaMemcpy(m->d_p, p.data(), m->P * 4, cudaMemcpyHostToDevice);
+    cudaMemset(m->d_m, 0, m->P * 4);
+    cudaMemset(m->d_v, 0, m->P * 4);
+    cudaMemset(m->d_err, 0, sizeof(unsigned));
+    refresh(m, 0);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        mlp_destroy(m);
+        return HB_ERR_CUDA;
+    }
+    *out = m;
+    return HB_OK;
+}
+
+hb_status mlp_destroy(hb_mlp_handle m) {
+    if (!m) return HB_ERR_INVALID_ARG;
+    free_ws(m);
+    cudaFree(m->d_p); cudaFree(m->d_m); cudaFree(m->d_v); cudaFree(m->d_g); cudaFree(m->d_loss);
+    cudaFree(m->W1b); cudaFree(m->W2b); cudaFree(m->W2tb); cudaFree(m->d_err);
+    delete m;
+    return HB_OK;
+}
+
+hb_status mlp_param_count(hb_mlp_handle m, uint64_t *P) {
+    if (!m || !P) return HB_ERR_INVALID_ARG;
+    *P = m->P;
+    return HB_OK;
+}
+
+hb_status mlp_get_params(hb_mlp_handle m, float *host) {
+    if (!m || !host) return HB_ERR_INVALID_ARG;
+    PD_CUDA(cudaMemcpy(host, m->d_p, m->P * 4, cudaMemcpyDeviceToHost));
+    return HB_OK;
+}
+
+hb_status mlp_set_params(hb_mlp_handle m, const float *host) {
+    if (!m || !host) return HB_ERR_INVALID_ARG;
+    PD_CUDA(cudaMemcpy(m->d_p, host, m->P * 4, cudaMemcpyHostToDevice));
+    refresh(m, 0);
+    PD_CUDA(cudaDeviceSynchronize());
+    return HB_OK;
+}
+
+hb_status mlp_forward(hb_mlp_handle m, const uint64_t *states, uint64_t n, float *out, void *stream) {
+    if (!m || (n > 0 && (!states || !out))) return HB_ERR_INVALID_ARG;
+    if (n == 0) return HB_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t n_pad = (n + kBM - 1) / kBM * kBM;
+    hb_status s = ensure_ws(m, n_pad);
+    if (s != HB_OK) return s;
+    k_bits<<<grid_of(n_pad * kIn, m->sm_count), 256, 0, st>>>(states, n, n_pad, m->n_in, m->X);
+    if ((s = forward_rows(m, n, n_pad, st)) != HB_OK) return s;
+    PD_CUDA(cudaMemcpyAsync(out, m->out, n * 8, cudaMemcpyDeviceToDevice, st));
+    return HB_OK;
+}
+
+hb_status mlp_gradient(hb_mlp_handle m, const uint64_t *states, uint64_t n, const float *t_log, const float *t_sign,
+                       const float *weights, float lam, float *grad, float *loss, void *stream) {
+    if (!m || !states || !t_log || !t_sign || !weights || n == 0) return HB_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t n_pad = (n + kBM - 1) / kBM * kBM;
+    hb_status s = ensure_ws(m, n_pad);
+    if (s != HB_OK) return s;
+    k_bits<<<grid_of(n_pad * kIn, m->sm_count), 256, 0, st>>>(states, n, n_pad, m->n_in, m->X);
+    if ((s = forward_rows(m, n, n_pad, st)) != HB_OK) return s;
+    PD_CUDA(cudaMemsetAsync(m->d_g, 0, m->P * 4, st));
+    PD_CUDA(cudaMemsetAsync(m->d_loss, 0, 4, st));
+    k_output_back<<<grid_of(n_pad, m->sm_count), 256, 0, st>>>(
+        m->Z2, m->d_p + m->ob2, m->d_p + m->oW3, m->out, t_log, t_sign, weights, lam, n, n_pad, m->dZ2, m->dZ2T,
+        m->d_g + m->oW3, m->d_g + m->ob3, m->d_g + m->ob2, m->d_loss);
+    // dA1 = dZ2 W2  (B = W2^T rows: [in][out])
+    if ((s = gemm(m, m->dZ2, kH, m->W2tb, kH, m->dA1, kH, (int)n_pad, kH, kH, kH, 0, 1, st)) != HB_OK) return s;
+    k_hidden_back<<<grid_of(n_pad * kH, m->sm_count), 256, 0, st>>>(m->dA1, m->Z1, m->d_p + m->ob1, n, n_pad, m->dZ1T,
+                                                                    m->d_g + m->ob1);
+    // gW2 = dZ2^T A1 and gW1 = dZ1^T X: K runs over the batch, split over CTAs, atomically accumulated
+    k_transpose_bf16<<<grid_of(n_pad * kH, m->sm_count), 256, 0, st>>>(m->A1, n_pad, kH, m->A1T);
+    k_transpose_bf16<<<grid_of(n_pad * kIn, m->sm_count), 256, 0, st>>>(m->X, n_pad, kIn, m->XT);
+    const int split = (int)std::max<uint64_t>(1, std::min<uint64_t>(n_pad / 512, (uint64_t)m->sm_count * 2));
+    if ((s = gemm(m, m->dZ2T, (int)n_pad, m->A1T, (int)n_pad, m->d_g + m->oW2, kH, kH, kH, (int)n_pad, kH, 1, split,
+                  st)) != HB_OK)
+        return s;
+    if ((s = gemm(m, m->dZ1T, (int)n_pad, m->XT, (int)n_pad, m->d_g + m->oW1, m->n_in, kH, kIn, (int)n_pad, m->n_in, 1,
+                  split, st)) != HB_OK)
+        return s;
+    if (grad) PD_CUDA(cudaMemcpyAsync(grad, m->d_g, m->P * 4, cudaMemcpyDeviceToDevice, st));
+    if (loss) PD_CUDA(cudaMemcpyAsync(loss, m->d_loss, 4, cudaMemcpyDeviceToDevice, st));
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+hb_status mlp_adam_step(hb_mlp_handle m, float lr, void *stream) {
+    if (!m || !(lr > 0)) return HB_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    m->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
+    k_adam<<<grid_of(m->P, m->sm_count), 256, 0, st>>>(m->d_p, m->d_g, m->d_m, m->d_v, m->P, lr, b1, b2, 1e-8f, c1, c2);
+    refresh(m, st);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+hb_status mlp_start_vector(hb_mlp_handle m, hb_handle h, hb_dtype dt, void *v, void *stream) {
+    if (!m || !h || !v || (dt != HB_F64 && dt != HB_F32 && dt != HB_FX64)) return HB_ERR_INVALID_ARG;
+    if (2 * h->L != m->n_in) return HB_ERR_INVALID_ARG;
+    hb_status s = pd_build_tables(h);
+    if (s != HB_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t chunk = 1ull << 20;
+    if ((s = ensure_ws(m, chunk)) != HB_OK) return s;
+    for (uint64_t i0 = 0; i0 < h->D; i0 += chunk) {
+        const uint64_t n = std::min(chunk, h->D - i0);
+        const uint64_t n_pad = (n + kBM - 1) / kBM * kBM;
+        k_states_of_range<<<grid_of(n, m->sm_count), 256, 0, st>>>(h->up.str, h->dn.str, h->D_dn, h->L, i0, n,
+                                                                   m->states);
+        k_bits<<<grid_of(n_pad * kIn, m->sm_count), 256, 0, st>>>(m->states, n, n_pad, m->n_in, m->X);
+        if ((s = forward_rows(m, n, n_pad, st)) != HB_OK) return s;
+        if (dt == HB_F32)
+            k_start_values<float><<<grid_of(n, m->sm_count), 256, 0, st>>>(m->out, n, static_cast<float *>(v) + i0, 0);
+        else if (dt == HB_F64)
+            k_start_values<double><<<grid_of(n, m->sm_count), 256, 0, st>>>(m->out, n, static_cast<double *>(v) + i0, 0);
+        else
+            k_start_values<int64_t><<<grid_of(n, m->sm_count), 256, 0, st>>>(m->out, n,
+                                                                             static_cast<int64_t *>(v) + i0, h->fx_frac);
+    }
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+hb_status mlp_last_error(hb_mlp_handle m) {
+    if (!m) return HB_ERR_INVALID_ARG;
+    PD_CUDA(cudaDeviceSynchronize());
+    unsigned bits = 0;
+    PD_CUDA(cudaMemcpy(&bits, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    PD_CUDA(cudaMemset(m->d_err, 0, sizeof(unsigned)));
+    for (int s = 1; s <= (int)HB_ERR_TIMEOUT; ++s)
+        if (bits & PD_ERRBIT(s)) return (hb_status)s;
+    return HB_OK;
+}
+
+// C[M, N] = A[M, K] B[N, K]^T on the tensor cores (bf16 in, f32 out), exposed for tests.
+hb_status mlp_tc_gemm(const void *A, const void *B, float *C, int M, int N, int K, void *stream) {
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || K % 8 != 0 || (N != 32 && N % 128 != 0)) return HB_ERR_INVALID_ARG;
+    hb_mlp tmp;
+    unsigned *err = nullptr;
+    PD_CUDA(cudaMalloc(&err, sizeof(unsigned)));
+    cudaMemset(err, 0, sizeof(unsigned));
+    cudaGetDevice(&tmp.device);
+    cudaDeviceGetAttribute(&tmp.sm_count, cudaDevAttrMultiProcessorCount, tmp.device);
+    tmp.d_err = err;
+    hb_status s = gemm(&tmp, static_cast<const __nv_bfloat16 *>(A), K, static_cast<const __nv_bfloat16 *>(B), K, C, N, M,
+                       N, K, N, 0, 1, reinterpret_cast<cudaStream_t>(stream));
+    cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    unsigned bits = 0;
+    cudaMemcpy(&bits, err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    tmp.d_err = nullptr;
+    if (s == HB_OK && bits) s = HB_ERR_TIMEOUT;
+    return s;
+}
+
+}  // extern "C"
