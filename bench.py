@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="hubbard4x4_half", choices=sorted(WORKLOADS) + ["batch64"])
+    p.add_argument("--workload", default="hubbard4x4_half", choices=sorted(WORKLOADS) + ["batch64", "learned4x4"])
     p.add_argument("--dtype", default="f64", choices=["f64", "fx64", "f32"],
                    help="Krylov vector type: float64 (float64 FMAs), fixed-point int64, float32")
     p.add_argument("--no-solve", action="store_true", help="skip the time-to-E0 runs")
@@ -448,9 +448,59 @@ def run_batch(args, world, rank, local):
         h.close()
 
 
+def run_learned(args, world, rank, local):
+    """Learned start vector on the 4x4 t-t' cluster: train at U in {2,4,6,10} (half filling), then
+    iterations and wall time to E0 at 1e-10 at U in {3,5,8,12} and in the doped (7,7) sector at U=8."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1707_03974_gb300.build import build
+    build()
+    import paper_1707_03974_gb300 as pd
+    from paper_1707_03974_gb300 import learned
+    import workloads as wl
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    t0 = time.perf_counter()
+    sets = []
+    for U in (2.0, 4.0, 6.0, 10.0):
+        h = pd.Handle(cl.L, cl.bonds, cl.t, U, 8, 8)
+        _, psi = learned.ground_state(h, tol=1e-6)
+        sets.append(learned.sample(h, psi, 500000, g))
+        del psi
+        h.close()
+    t_data = time.perf_counter() - t0
+    m = pd.Mlp(32, seed=1)
+    rep = learned.train(m, sets, steps=max(200, args.steps * 50), batch=32768, lr=2e-3)
+    cases = {}
+    for U, nu, nd in ((3.0, 8, 8), (5.0, 8, 8), (8.0, 8, 8), (12.0, 8, 8), (8.0, 7, 7)):
+        h = pd.Handle(cl.L, cl.bonds, cl.t, U, nu, nd)
+        _, psi = learned.ground_state(h, tol=1e-7)
+        res = learned.compare(m, h, psi, seeds=(0, 1))
+        cases[f"U{U:g}_{nu}_{nd}"] = res
+        del psi
+        h.close()
+        torch.cuda.empty_cache()
+    rnd = [min(r["iterations"] for r in c["random_f64"]) for c in cases.values()]
+    lrn = [c["learned_f64"]["iterations"] for c in cases.values()]
+    out = {"metric": "Lanczos iterations to E0 at 1e-10, learned start / random start (4x4 t-t', unseen U and doped)",
+           "value": round(sum(lrn) / sum(rnd), 4), "unit": "ratio", "n_gpus": 1, "higher_is_better": False,
+           "dtype": "bf16 network (tcgen05), f64/int64 Lanczos", "data": "synthetic (method's own ground states)",
+           "config": {"workload": "learned start vector", "train_U": [2, 4, 6, 10], "train_samples_per_U": 500000,
+                      "hidden": 128, "steps": len(rep.losses) and max(200, args.steps * 50), "batch": 32768},
+           "train_loss_first_last": [rep.losses[0], rep.losses[-1]], "train_seconds": round(rep.seconds, 3),
+           "data_seconds": round(t_data, 3), "cases": cases}
+    print(json.dumps(out))
+    m.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.workload == "learned4x4" and args.impl == "ours":
+        if rank == 0:
+            run_learned(args, world, rank, local)
+        return
     if args.workload == "batch64" and args.impl == "ours":
         if rank == 0:
             run_batch(args, world, rank, local)

@@ -253,6 +253,17 @@ hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *v, const vo
                                const double *beta_prev, double *alpha, double *beta, void *ev_hv_begin,
                                void *ev_hv_end, uint32_t *launches, void *stream);
 
+/*
+ * float32 Lanczos (float64 scalars) to opts->tol, then the normalised Ritz
+ * vector of E0, written to ritz (device float[D]) by replaying the recurrence
+ * from the stored start vector with the recorded alpha, beta.  Workspace as
+ * lanczos_workspace_bytes for vec_dtype HB_F32 with fp64_finish = 1.  Used to
+ * produce training targets for the start-vector network.  Synchronises.
+ */
+hb_status lanczos_ritz_vector_f32(hb_handle h, const hb_lanczos_opts *opts, const void *v0, void *workspace,
+                                  uint64_t workspace_bytes, float *ritz, double *E0, hb_lanczos_info *info,
+                                  void *stream);
+
 /* ---------------- batches of independent problems ---------------- */
 /*
  * A batch groups handles (different clusters, sectors, U) that are applied and

@@ -77,6 +77,19 @@ def load():
                                                 ctypes.POINTER(D), ctypes.POINTER(LanczosInfo), P]),
         "hb_tridiag_lowest": (ctypes.c_int, [P, P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "hubbard_fixed_point_bits": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "lanczos_ritz_vector_f32": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, P, U64, P,
+                                                   ctypes.POINTER(D), ctypes.POINTER(LanczosInfo), P]),
+        "mlp_create": (ctypes.c_int, [I32, U64, ctypes.POINTER(P)]),
+        "mlp_destroy": (ctypes.c_int, [P]),
+        "mlp_param_count": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
+        "mlp_get_params": (ctypes.c_int, [P, P]),
+        "mlp_set_params": (ctypes.c_int, [P, P]),
+        "mlp_forward": (ctypes.c_int, [P, P, U64, P, P]),
+        "mlp_gradient": (ctypes.c_int, [P, P, U64, P, P, P, ctypes.c_float, P, P, P]),
+        "mlp_adam_step": (ctypes.c_int, [P, ctypes.c_float, P]),
+        "mlp_start_vector": (ctypes.c_int, [P, P, I32, P, P]),
+        "mlp_last_error": (ctypes.c_int, [P]),
+        "mlp_tc_gemm": (ctypes.c_int, [P, P, P, I32, I32, I32, P]),
         "hubbard_batch_create": (ctypes.c_int, [I32, P, ctypes.POINTER(P)]),
         "hubbard_batch_destroy": (ctypes.c_int, [P]),
         "hubbard_batch_layout": (ctypes.c_int, [P, P]),
@@ -369,6 +382,26 @@ def lanczos_step_noalloc(h: Handle, v, vprev, w, beta_prev, alpha, beta, ev_hv_b
                                        _stream_ptr(stream)), "lanczos_step_noalloc")
 
 
+def lanczos_ritz_vector_f32(h: Handle, maxit: int = 1000, tol: float = 1e-6, seed: int = 0, v0=None,
+                            check_every: int = 1, stream=None):
+    """(E0, normalised float32 ground-state vector, info dict) from float32 Lanczos + replay."""
+    import torch
+    o = LanczosOpts(int(maxit), 0, HB_F32, int(check_every), float(tol), int(seed) & ((1 << 64) - 1), 1, 0)
+    lib = load()
+    nb = ctypes.c_uint64()
+    _check(lib.lanczos_workspace_bytes(h.ptr, ctypes.byref(o), ctypes.byref(nb)), "lanczos_workspace_bytes")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ws = torch.empty((nb.value,), dtype=torch.uint8, device=dev)
+    ritz = torch.empty(h.D, dtype=torch.float32, device=dev)
+    E0 = ctypes.c_double()
+    info = LanczosInfo()
+    st = lib.lanczos_ritz_vector_f32(h.ptr, ctypes.byref(o), _ptr(v0), _ptr(ws), nb.value, _ptr(ritz),
+                                     ctypes.byref(E0), ctypes.byref(info), _stream_ptr(stream))
+    if st not in (0, 7):
+        raise HubbardError(st, "lanczos_ritz_vector_f32")
+    return E0.value, ritz, {"iterations": info.iterations, "residual": info.residual, "converged": bool(info.converged)}
+
+
 def hb_tridiag_lowest(alpha, beta):
     """Host utility of the library: lowest eigenvalue of a tridiagonal and its eigenvector's last entry."""
     import numpy as np
@@ -454,3 +487,94 @@ def lanczos_batch_ground_state(b: Batch, maxit: int = 1000, tol: float = 1e-10, 
         raise HubbardError(st, "lanczos_batch_ground_state")
     return E0.tolist(), [{"E0": i.E0, "residual": i.residual, "iterations": i.iterations,
                           "converged": bool(i.converged), "seconds": i.seconds} for i in infos], STATUS[st]
+
+
+# ---------------------------------------------------------------- learned start vector (paradeisos_mlp.h)
+
+class Mlp:
+    """Owns an hb_mlp_handle (mlp_create / mlp_destroy)."""
+
+    def __init__(self, n_in: int, seed: int = 0):
+        lib = load()
+        m = ctypes.c_void_p()
+        _check(lib.mlp_create(int(n_in), int(seed) & ((1 << 64) - 1), ctypes.byref(m)), "mlp_create")
+        self._m = m
+        self.n_in = int(n_in)
+        P = ctypes.c_uint64()
+        _check(lib.mlp_param_count(m, ctypes.byref(P)), "mlp_param_count")
+        self.P = P.value
+
+    @property
+    def ptr(self):
+        if self._m is None:
+            raise RuntimeError("network destroyed")
+        return self._m
+
+    def close(self):
+        if getattr(self, "_m", None) is not None:
+            load().mlp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        import numpy as np
+        a = np.zeros(self.P, dtype=np.float32)
+        _check(load().mlp_get_params(self.ptr, ctypes.c_void_p(a.ctypes.data)), "mlp_get_params")
+        return a
+
+    def set_params(self, a):
+        import numpy as np
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        if a.size != self.P:
+            raise ValueError("parameter vector has the wrong length")
+        _check(load().mlp_set_params(self.ptr, ctypes.c_void_p(a.ctypes.data)), "mlp_set_params")
+
+
+def mlp_forward(m: Mlp, states, stream=None):
+    import torch
+    _need_cuda(states)
+    out = torch.empty((states.numel(), 2), dtype=torch.float32, device=states.device)
+    _check(load().mlp_forward(m.ptr, _ptr(states), states.numel(), _ptr(out), _stream_ptr(stream)), "mlp_forward")
+    return out
+
+
+def mlp_gradient(m: Mlp, states, t_log, t_sign, weights, lam: float = 1.0, stream=None):
+    """Returns (grad tensor [P], loss tensor [1]); the gradient is also kept for mlp_adam_step."""
+    import torch
+    _need_cuda(states, t_log, t_sign, weights)
+    g = torch.empty(m.P, dtype=torch.float32, device=states.device)
+    loss = torch.empty(1, dtype=torch.float32, device=states.device)
+    _check(load().mlp_gradient(m.ptr, _ptr(states), states.numel(), _ptr(t_log), _ptr(t_sign), _ptr(weights),
+                               float(lam), _ptr(g), _ptr(loss), _stream_ptr(stream)), "mlp_gradient")
+    return g, loss
+
+
+def mlp_adam_step(m: Mlp, lr: float, stream=None):
+    _check(load().mlp_adam_step(m.ptr, float(lr), _stream_ptr(stream)), "mlp_adam_step")
+
+
+def mlp_start_vector(m: Mlp, h: Handle, dtype, stream=None):
+    import torch
+    v = torch.empty(h.D, dtype=dtype, device=torch.device("cuda", torch.cuda.current_device()))
+    _check(load().mlp_start_vector(m.ptr, h.ptr, _dtype_code(v), _ptr(v), _stream_ptr(stream)), "mlp_start_vector")
+    return v
+
+
+def mlp_last_error(m: Mlp) -> str:
+    return STATUS[load().mlp_last_error(m.ptr)]
+
+
+def mlp_tc_gemm(A, B, stream=None):
+    """C = A @ B^T on the library's tcgen05 kernel (A [M,K], B [N,K] bfloat16 CUDA tensors)."""
+    import torch
+    _need_cuda(A, B)
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(load().mlp_tc_gemm(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), _stream_ptr(stream)), "mlp_tc_gemm")
+    return C

@@ -649,6 +649,39 @@ hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, b
     return HB_OK;
 }
 
+
+// Ritz vector y = sum_k s_k v_k of a float32 run: replay the recurrence from
+// the stored start vector with the recorded alpha, beta (three slots: V slots
+// 1, 2 and the start copy), accumulating y in V slot 0.  The replayed vectors
+// are bit-identical to the first pass (same kernels, same scalars).
+hb_status replay_ritz_f32(Solve &s, const PhaseResult &r, float *start_copy, float *V, uint64_t stride) {
+    const uint64_t D = s.D;
+    const int m = r.iters;
+    std::vector<double> svec;
+    double th, sl;
+    tridiag_lowest_host(r.alpha.data(), r.beta.data(), m, &th, &sl, &svec);
+    float *y = V;
+    float *a = V + 1 * stride, *b = V + 2 * stride;
+    float *vj = start_copy, *vp = nullptr, *wbuf = a, *spare = b;
+    PD_CUDA(cudaMemsetAsync(y, 0, D * 4, s.st));
+    for (int k = 0; k < m; ++k) {
+        k_axpy_scalar_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(y, vj, (float)svec[k], D);
+        if (k + 1 == m) break;
+        hb_status st = pd_apply(s.h, HB_F32, vj, wbuf, s.st);
+        if (st != HB_OK) return st;
+        const double bk = r.beta[k];
+        k_regen_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(wbuf, vj, vp, (float)r.alpha[k],
+                                                          k > 0 ? (float)r.beta[k - 1] : 0.f,
+                                                          bk != 0 ? (float)(1.0 / bk) : 0.f, D);
+        float *old_vp = vp ? vp : spare;  // rotate: vp <- vj, vj <- wbuf, wbuf <- old vp
+        vp = vj;
+        vj = wbuf;
+        wbuf = old_vp;
+    }
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -782,33 +815,10 @@ hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *o, const void
         st = lanczos_run<float>(s, HB_F32, V, stride, o->maxit, reorth, tol32, o->check_every, r);
         iters_f32 = r.iters;
         if (st == HB_OK && finish && !(r.converged && tol32 <= tol)) {
-            // Ritz vector y = sum_k s_k v_k: replay the float32 recurrence with the
-            // recorded alpha, beta (three slots) and accumulate into the start copy's
-            // successor slot; then continue in float64 from y.
+            // Ritz vector of the float32 phase into slot 0, then continue in float64 / fixed point
             const int m = r.iters;
-            std::vector<double> svec;
-            double th, sl;
-            tridiag_lowest_host(r.alpha.data(), r.beta.data(), m, &th, &sl, &svec);
-            float *y = V + 0 * stride;  // slot 0 becomes the accumulator
-            float *a = V + 1 * stride, *b = V + 2 * stride;
-            float *vj = start_copy, *vp = nullptr, *wbuf = a, *spare = b;
-            // y = s_0 v_0
-            cudaMemsetAsync(y, 0, D * 4, s.st);
-            for (int k = 0; k < m; ++k) {
-                k_axpy_scalar_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(y, vj, (float)svec[k], D);
-                if (k + 1 == m) break;
-                st = pd_apply(h, HB_F32, vj, wbuf, s.st);
-                if (st != HB_OK) return st;
-                const double bk = r.beta[k];
-                k_regen_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(wbuf, vj, vp, (float)r.alpha[k],
-                                                                  k > 0 ? (float)r.beta[k - 1] : 0.f,
-                                                                  bk != 0 ? (float)(1.0 / bk) : 0.f, D);
-                // rotate: vp <- vj, vj <- wbuf, wbuf <- old vp (or the spare slot)
-                float *old_vp = vp ? vp : spare;
-                vp = vj;
-                vj = wbuf;
-                wbuf = old_vp;
-            }
+            if ((st = replay_ritz_f32(s, r, start_copy, V, stride)) != HB_OK) return st;
+            float *y = V;
             PD_CUDA(cudaGetLastError());
             const uint64_t stride64 = align256(D * 8) / 8;
             const int rest = std::max(1, o->maxit - m);
@@ -842,6 +852,61 @@ hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *o, const void
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return outcome;
+}
+
+hb_status lanczos_ritz_vector_f32(hb_handle h, const hb_lanczos_opts *o, const void *v0, void *workspace,
+                                  uint64_t workspace_bytes, float *ritz, double *E0, hb_lanczos_info *info,
+                                  void *stream) {
+    if (!h || !o || !workspace || !ritz || !E0 || o->maxit < 1 || o->check_every < 1 || o->reorth)
+        return HB_ERR_INVALID_ARG;
+    hb_lanczos_opts oo = *o;
+    oo.vec_dtype = HB_F32;
+    oo.fp64_finish = 1;  // same workspace layout (keeps the start copy)
+    const Layout L = make_layout(h, oo);
+    if (workspace_bytes < L.total) return HB_ERR_NO_MEMORY;
+    if ((uintptr_t)workspace % 256 != 0) return HB_ERR_INVALID_ARG;
+    hb_status st = pd_build_tables(h);
+    if (st != HB_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    char *ws = static_cast<char *>(workspace);
+    Solve s;
+    s.h = h;
+    s.st = reinterpret_cast<cudaStream_t>(stream);
+    s.D = h->D;
+    s.nblk = L.nblk;
+    s.partials = reinterpret_cast<double *>(ws + L.partials);
+    s.d_alpha = reinterpret_cast<double *>(ws + L.scal);
+    s.d_beta = s.d_alpha + (oo.maxit + 1);
+    s.d_coef = s.d_beta + (oo.maxit + 1);
+    s.d_misc = s.d_coef + (oo.maxit + 1);
+    s.grid_vec = h->sm_count * 8;
+    const uint64_t D = h->D, stride = align256(D * 4) / 4;
+    float *V = reinterpret_cast<float *>(ws + L.vec);
+    float *start_copy = reinterpret_cast<float *>(ws + L.vec2);
+    if (v0)
+        k_copy_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(static_cast<const float *>(v0), V, D);
+    else
+        k_fill_random<float><<<s.grid_vec, kRedThreads, 0, s.st>>>(V, D, oo.seed);
+    if ((st = normalise(s, V)) != HB_OK) return st;
+    k_copy_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(V, start_copy, D);
+    PhaseResult r;
+    st = lanczos_run<float>(s, HB_F32, V, stride, oo.maxit, false, oo.tol, oo.check_every, r);
+    if (st != HB_OK) return st;
+    if ((st = replay_ritz_f32(s, r, start_copy, V, stride)) != HB_OK) return st;
+    if ((st = normalise(s, V)) != HB_OK) return st;
+    k_copy_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(V, ritz, D);
+    PD_CUDA(cudaStreamSynchronize(s.st));
+    *E0 = r.theta;
+    if (info) {
+        info->E0 = r.theta;
+        info->residual = r.res;
+        info->iterations = r.iters;
+        info->iterations_f32 = r.iters;
+        info->status = r.converged ? HB_OK : HB_ERR_NOT_CONVERGED;
+        info->converged = r.converged;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return r.converged ? HB_OK : HB_ERR_NOT_CONVERGED;
 }
 
 }  // extern "C"

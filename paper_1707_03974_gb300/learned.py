@@ -1,0 +1,129 @@
+"""Learned Lanczos start vectors: training and evaluation driver over the C ABI.
+
+Not part of the paper.  The network (include/paradeisos_mlp.h) is trained on
+ground states that the library computes itself (float32 Lanczos + Ritz vector)
+at a few values of U, then used to build the start vector of the float64-grade
+Lanczos solve at other U or another sector.  Training samples are basis states
+drawn with probability |psi|^2 (inverse-CDF sampling), targets are
+log|psi| (shifted to zero mean per training problem) and the sign of psi with
+the global sign fixed by the largest entry.  Everything numerical runs in the
+library's kernels; torch provides memory, random numbers and the sampling
+bookkeeping.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Sequence
+
+from . import _binding as B
+
+
+@dataclass
+class TrainingSet:
+    states: "object"   # int64 CUDA tensor of combined strings
+    t_log: "object"    # float32
+    t_sign: "object"   # float32, +-1
+
+
+@dataclass
+class TrainReport:
+    losses: List[float] = field(default_factory=list)
+    seconds: float = 0.0
+
+
+def ground_state(h: B.Handle, tol: float = 1e-6, maxit: int = 2000, seed: int = 0):
+    """(E0, normalised float32 ground-state vector) by float32 Lanczos and the replayed Ritz vector."""
+    E0, psi, _ = B.lanczos_ritz_vector_f32(h, maxit=maxit, tol=tol, seed=seed)
+    return E0, psi
+
+
+def sample(h: B.Handle, psi, n: int, generator) -> TrainingSet:
+    """n basis states drawn with probability psi^2, with their log-amplitude and sign targets."""
+    import torch
+    p = psi.double()
+    k = int(torch.argmax(p.abs()).item())
+    if p[k] < 0:
+        p = -p
+    cdf = torch.cumsum(p * p, 0)
+    u = torch.rand(n, generator=generator, device=psi.device, dtype=torch.float64) * cdf[-1]
+    idx = torch.searchsorted(cdf, u).clamp_(max=h.D - 1)
+    states = B.paradeisos_unrank(h, idx.to(torch.int64))
+    amp = p[idx]
+    t_log = torch.log(amp.abs().clamp_min(1e-300))
+    t_log = (t_log - t_log.mean()).float()
+    t_sign = torch.where(amp >= 0, 1.0, -1.0).float()
+    return TrainingSet(states, t_log, t_sign)
+
+
+def train(m: B.Mlp, sets: Sequence[TrainingSet], steps: int, batch: int = 32768, lr: float = 2e-3,
+          lam: float = 1.0, seed: int = 0) -> TrainReport:
+    import torch
+    states = torch.cat([s.states for s in sets])
+    t_log = torch.cat([s.t_log for s in sets])
+    t_sign = torch.cat([s.t_sign for s in sets])
+    g = torch.Generator(device=states.device)
+    g.manual_seed(seed)
+    w = torch.full((batch,), 1.0 / batch, dtype=torch.float32, device=states.device)
+    rep = TrainReport()
+    t0 = time.perf_counter()
+    for it in range(steps):
+        sel = torch.randint(0, states.numel(), (batch,), generator=g, device=states.device)
+        _, loss = B.mlp_gradient(m, states[sel].contiguous(), t_log[sel].contiguous(), t_sign[sel].contiguous(), w, lam)
+        step_lr = lr * (0.5 * (1 + __import__("math").cos(__import__("math").pi * it / steps)))
+        B.mlp_adam_step(m, max(step_lr, lr * 0.02))
+        if it % 25 == 0 or it == steps - 1:
+            rep.losses.append(float(loss.item()))
+    torch.cuda.synchronize()
+    rep.seconds = time.perf_counter() - t0
+    return rep
+
+
+def overlap(m: B.Mlp, h: B.Handle, psi) -> float:
+    """|<v0 / |v0|, psi>| of the network's start vector with a normalised reference vector."""
+    import torch
+    v = B.mlp_start_vector(m, h, torch.float32).double()
+    return float((torch.dot(v, psi.double()) / v.norm()).abs().item())
+
+
+def solve_from(h: B.Handle, dtype, v0=None, seed: int = 0, tol: float = 1e-10, fp64_finish=False) -> Dict:
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = B.lanczos_ground_state(h, maxit=3000, tol=tol, dtype=dtype, v0=v0, seed=seed, fp64_finish=fp64_finish,
+                               raise_on_error=False)
+    torch.cuda.synchronize()
+    return {"E0": r.E0, "iterations": r.iterations, "iterations_f32": r.iterations_f32, "converged": r.converged,
+            "seconds": time.perf_counter() - t0}
+
+
+def compare(m: B.Mlp, h: B.Handle, psi=None, seeds=(0,)) -> Dict:
+    """Iterations and wall time to E0 at 1e-10: learned start vs random starts (float64 and fixed point),
+    plus the mixed float32 + fixed-point solve from the learned start (start-vector build time included)."""
+    import torch
+    out = {"random_f64": [solve_from(h, torch.float64, seed=s) for s in seeds]}
+    out["random_fx64"] = [solve_from(h, torch.int64, seed=s) for s in seeds]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    v64 = B.mlp_start_vector(m, h, torch.float64)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    r = solve_from(h, torch.float64, v0=v64)
+    r["seconds"] += t_build
+    out["learned_f64"] = r
+    t0 = time.perf_counter()
+    vfx = B.mlp_start_vector(m, h, torch.int64)
+    torch.cuda.synchronize()
+    r = solve_from(h, torch.int64, v0=vfx)
+    r["seconds"] += time.perf_counter() - t0
+    out["learned_fx64"] = r
+    t0 = time.perf_counter()
+    v32 = B.mlp_start_vector(m, h, torch.float32)
+    torch.cuda.synchronize()
+    r = solve_from(h, torch.float32, v0=v32, fp64_finish="fx64")
+    r["seconds"] += time.perf_counter() - t0
+    out["learned_mixed_f32_fx64"] = r
+    out["start_vector_seconds"] = t_build
+    if psi is not None:
+        out["overlap"] = overlap(m, h, psi)
+    return out

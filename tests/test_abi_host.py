@@ -21,8 +21,8 @@ def lib():
     return pd.load()
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:hb_status|const char \*)\s*(\w+)\s*\(", text, flags=re.M)))
 
@@ -33,6 +33,13 @@ def test_every_declared_symbol_is_exported(lib):
     for n in names:
         assert hasattr(lib, n), n
     assert set(names) == set(pd.EXPORTED_SYMBOLS)
+
+
+def test_every_mlp_symbol_is_exported(lib):
+    names = declared_functions(os.path.join(ROOT, "include", "paradeisos_mlp.h"))
+    assert set(names) == set(pd.MLP_SYMBOLS)
+    for n in names:
+        assert hasattr(lib, n), n
 
 
 def test_status_strings(lib):

@@ -1,0 +1,87 @@
+"""Start-vector network on the GPU vs the CPU oracle (bf16 operands, f32 accumulation)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle.basis import Basis
+from oracle.mlp import bits_of, forward, loss_and_grad
+from tests.gpu_util import need_gpu, to_dev_u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    return torch, pd
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 128, 32), (384, 32, 128), (128, 128, 1024), (1000, 128, 128)])
+def test_tc_gemm_matches_float_reference(env, M, N, K):
+    torch, pd = env
+    g = torch.Generator().manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    C = pd.mlp_tc_gemm(A.cuda(), B.cuda()).cpu()
+    ref = A.double() @ B.double().T   # exact products of bf16 values, float64 sums
+    err = (C.double() - ref).abs().max().item()
+    assert err <= 2e-6 * K * max(1.0, ref.abs().max().item() / K) + 1e-5 * ref.abs().max().item()
+
+
+def test_forward_matches_oracle(env):
+    torch, pd = env
+    L = 8
+    m = pd.Mlp(2 * L, seed=3)
+    theta = m.get_params().astype(np.float64)
+    b = Basis(L, 4, 3)
+    states = b.combined[:777]
+    out = pd.mlp_forward(m, to_dev_u64(states)).cpu().numpy()
+    ref, _ = forward(theta, bits_of(states, L), 2 * L, 128, emulate_bf16=True)
+    assert np.max(np.abs(out - ref)) <= 2e-3 * max(1.0, np.max(np.abs(ref)))
+    assert pd.mlp_last_error(m) == "HB_OK"
+    m.close()
+
+
+def test_gradient_matches_oracle(env):
+    torch, pd = env
+    L = 8
+    m = pd.Mlp(2 * L, seed=4)
+    theta = m.get_params().astype(np.float64)
+    b = Basis(L, 4, 4)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(b.D, 1500, replace=False)
+    states = b.combined[idx]
+    t_log = rng.normal(size=idx.size) - 4.0
+    t_sign = np.where(rng.random(idx.size) < 0.5, -1.0, 1.0)
+    w = rng.random(idx.size)
+    w /= w.sum()
+    dev = lambda a: torch.from_numpy(np.asarray(a, dtype=np.float32)).cuda()
+    g, loss = pd.mlp_gradient(m, to_dev_u64(states), dev(t_log), dev(t_sign), dev(w), lam=1.0)
+    g = g.cpu().numpy().astype(np.float64)
+    lref, gref = loss_and_grad(theta, bits_of(states, L), t_log, t_sign, w, 2 * L, 128, lam=1.0, emulate_bf16=True)
+    assert abs(loss.item() - lref) <= 1e-3 * abs(lref)
+    # bf16 rounding of the back-propagated activations: a few parts in a thousand
+    assert np.linalg.norm(g - gref) <= 2e-2 * np.linalg.norm(gref)
+    assert pd.mlp_last_error(m) == "HB_OK"
+    m.close()
+
+
+def test_training_reduces_loss(env):
+    torch, pd = env
+    L = 8
+    m = pd.Mlp(2 * L, seed=5)
+    b = Basis(L, 4, 4)
+    rng = np.random.default_rng(1)
+    states = to_dev_u64(b.combined)
+    bits = bits_of(b.combined, L)
+    t_log = torch.from_numpy((bits[:, :L].sum(1) - bits[:, L:].sum(1) * 0.5 - 3.0).astype(np.float32)).cuda()
+    t_sign = torch.from_numpy(np.where(bits[:, 0] > 0, 1.0, -1.0).astype(np.float32)).cuda()
+    w = torch.full((b.D,), 1.0 / b.D, dtype=torch.float32, device="cuda")
+    losses = []
+    for _ in range(60):
+        _, loss = pd.mlp_gradient(m, states, t_log, t_sign, w)
+        losses.append(loss.item())
+        pd.mlp_adam_step(m, 3e-3)
+    assert losses[-1] < 0.2 * losses[0]
+    m.close()
