@@ -42,7 +42,7 @@ hb_status mlp_gradient(hb_mlp_handle m, const uint64_t *states, uint64_t n, cons
                        void *stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
 hb_status mlp_adam_step(hb_mlp_handle m, float lr, void *stream);
-/* Start vector over the whole basis of h (n_in must be 2L): v[I] = sign * exp(min(log|psi|, 20) - 20)
+/* Start vector over the whole basis of h (n_in must be 2L): v[I] = sign * exp(min(log|psi|, 10) - 10)
  * for every combined index I (states from the backward map), in dtype dt.  Not normalised. */
 hb_status mlp_start_vector(hb_mlp_handle m, hb_handle h, hb_dtype dt, void *v, void *stream);
 /* Sticky device error (HB_ERR_TIMEOUT if a tensor-core completion wait gave up); synchronises. */

@@ -33,11 +33,11 @@ class HubbardError(RuntimeError):
 
 class HvConfig(ctypes.Structure):
     _fields_ = [("rows_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("visit_order", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("visit_order", ctypes.c_int32), ("column_pairs", ctypes.c_int32), ("ms", ctypes.c_float)]
 
     def as_dict(self):
         return {"rows_per_cta": self.rows_per_cta, "threads_per_cta": self.threads_per_cta,
-                "visit_order": self.visit_order, "ms": self.ms}
+                "visit_order": self.visit_order, "column_pairs": self.column_pairs, "ms": self.ms}
 
 
 class LanczosOpts(ctypes.Structure):
@@ -240,8 +240,8 @@ def hubbard_get_hv_config(h: "Handle", dtype) -> dict:
     return c.as_dict()
 
 
-def hubbard_set_hv_config(h: "Handle", dtype, rows_per_cta=0, threads_per_cta=0, visit_order=1):
-    c = HvConfig(int(rows_per_cta), int(threads_per_cta), int(visit_order), 0.0)
+def hubbard_set_hv_config(h: "Handle", dtype, rows_per_cta=0, threads_per_cta=0, visit_order=1, column_pairs=0):
+    c = HvConfig(int(rows_per_cta), int(threads_per_cta), int(visit_order), int(column_pairs), 0.0)
     _check(load().hubbard_set_hv_config(h.ptr, _dtype_of(dtype), ctypes.byref(c)), "hubbard_set_hv_config")
 
 

@@ -56,6 +56,7 @@ struct HvConfig {
     int rows = 0;     // rows of x staged per CTA group (1, 2 or 4)
     int threads = 0;  // threads per CTA (multiple of 32, <= 1024)
     int order = 1;    // 1: reverse Cuthill-McKee row visiting order, 0: storage order
+    int pair = 0;     // fixed point: two adjacent columns per thread (16-byte accesses)
 };
 
 struct hb_basis {

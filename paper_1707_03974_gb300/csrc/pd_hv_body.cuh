@@ -282,3 +282,145 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
         }
     }
 }
+
+// Fixed-point group with two adjacent columns per thread (D_dn even): the
+// staged rows and the spin-up rows are read as 16-byte pairs, and the two
+// columns' spin-down hop lists are walked together, so each thread keeps twice
+// as many independent loads in flight.  Same arithmetic, same results as
+// hv_fx_group (integer sums are exact; the final products are per element).
+template <int R, int NC>
+__device__ __forceinline__ void hv_fx_group_pair(const FxArgs &a, const int64_t *__restrict__ x,
+                                                 int64_t *__restrict__ y, uint64_t g, unsigned char *smem) {
+    const uint64_t Dd = a.Dd;
+    const int zr = a.zmax_up > 0 ? a.zmax_up : 1;
+    const int64_t *s_kd = reinterpret_cast<const int64_t *>(smem);
+    const int *s_gd = reinterpret_cast<const int *>(smem + 8 * (PD_MAXL + 1));
+    size_t off = (8 * (PD_MAXL + 1) + 4 * (PD_MAXL + 1) + 15) & ~(size_t)15;
+    uint64_t *s_useg = reinterpret_cast<uint64_t *>(smem + off);
+    off = (off + 8 * R + 15) & ~(size_t)15;
+    uint32_t *s_ucol = reinterpret_cast<uint32_t *>(smem + off);
+    off = (off + (size_t)R * zr * 4 + 15) & ~(size_t)15;
+    int64_t *s_x = reinterpret_cast<int64_t *>(smem + off);
+
+    const uint64_t p0 = g * R;
+    const uint64_t left = a.Du - p0;
+    const int nr = left < (uint64_t)R ? (int)left : R;
+    uint64_t ur[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) ur[r] = r < nr ? (a.order ? (uint64_t)a.order[p0 + r] : p0 + r) : 0;
+    __syncthreads();
+    if (threadIdx.x < R) s_useg[threadIdx.x] = threadIdx.x < nr ? a.seg_up[ur[threadIdx.x]] : 0ull;
+    for (int e = threadIdx.x; e < R * zr; e += blockDim.x) {
+        const int r = e / zr, k = e - r * zr;
+        if (r < nr && k < a.zmax_up) {
+            const uint64_t u = a.order ? (uint64_t)a.order[p0 + r] : p0 + r;
+            s_ucol[e] = a.ft_up[(uint64_t)k * a.Du + u];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r >= nr) break;
+        const longlong2 *xr = reinterpret_cast<const longlong2 *>(x + ur[r] * Dd);
+        for (uint64_t p = threadIdx.x; p < Dd / 2; p += blockDim.x) {
+            const longlong2 v = xr[p];
+            s_x[(2 * p) * R + r] = v.x;
+            s_x[(2 * p + 1) * R + r] = v.y;
+        }
+    }
+    __syncthreads();
+    uint32_t su[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) su[r] = r < nr ? a.str_up[ur[r]] : 0u;
+
+    for (uint64_t p = threadIdx.x; p < Dd / 2; p += blockDim.x) {
+        const uint64_t d0 = 2 * p;
+        int64_t acc0[R][NC], acc1[R][NC];
+        int neg0[NC], neg1[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            neg0[c] = neg1[c] = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc0[r][c] = acc1[r][c] = 0;
+        }
+        // spin-down hops of columns d0 and d0+1, walked together
+        const uint64_t sg0 = a.seg_dn[d0], sg1 = a.seg_dn[d0 + 1];
+        uint64_t k0 = 0, k1 = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int n0 = (int)((sg0 >> (8 * c)) & 0xFFu), n1 = (int)((sg1 >> (8 * c)) & 0xFFu);
+            const int nmax = n0 > n1 ? n0 : n1;
+            for (int i0 = 0; i0 < nmax; i0 += 2) {
+                uint32_t e0[2], e1[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    if (i0 + i < n0) e0[i] = a.ft_dn[(k0 + i0 + i) * Dd + d0];
+                    if (i0 + i < n1) e1[i] = a.ft_dn[(k1 + i0 + i) * Dd + d0 + 1];
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    if (i0 + i < n0) {
+                        const int64_t m = (int64_t)((int32_t)e0[i] >> 31);
+                        const uint64_t dk = e0[i] & PD_TGT_MASK;
+                        neg0[c] += (int)(e0[i] >> 31);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) acc0[r][c] += s_x[dk * R + r] ^ m;
+                    }
+                    if (i0 + i < n1) {
+                        const int64_t m = (int64_t)((int32_t)e1[i] >> 31);
+                        const uint64_t dk = e1[i] & PD_TGT_MASK;
+                        neg1[c] += (int)(e1[i] >> 31);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) acc1[r][c] += s_x[dk * R + r] ^ m;
+                    }
+                }
+            }
+            k0 += n0;
+            k1 += n1;
+        }
+        // spin-up hops: 16-byte column pairs of the rows x[u', :]
+        int negA[R][NC];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t ug = s_useg[r];
+            int kk = 0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                negA[r][c] = 0;
+                const int n = (int)((ug >> (8 * c)) & 0xFFu);
+                for (int i0 = 0; i0 < n; i0 += 4) {
+                    longlong2 xv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (i0 + i < n)
+                            xv[i] = *reinterpret_cast<const longlong2 *>(
+                                x + (uint64_t)(s_ucol[r * zr + kk + i0 + i] & PD_TGT_MASK) * Dd + d0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (i0 + i < n) {
+                            const uint32_t e = s_ucol[r * zr + kk + i0 + i];
+                            const int64_t m = (int64_t)((int32_t)e >> 31);
+                            acc0[r][c] += xv[i].x ^ m;
+                            acc1[r][c] += xv[i].y ^ m;
+                            negA[r][c] += (int)(e >> 31);
+                        }
+                }
+                kk += n;
+            }
+        }
+        const uint32_t sd0 = a.str_dn[d0], sd1 = a.str_dn[d0 + 1];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r >= nr) continue;
+            const int dc0 = __popc(su[r] & sd0), dc1 = __popc(su[r] & sd1);
+            longlong2 o;
+            o.x = fx_mul(s_x[d0 * R + r], s_kd[dc0], s_gd[dc0]);
+            o.y = fx_mul(s_x[(d0 + 1) * R + r], s_kd[dc1], s_gd[dc1]);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                o.x += fx_mul(acc0[r][c] + neg0[c] + negA[r][c], a.Kc[c], a.Gc[c]);
+                o.y += fx_mul(acc1[r][c] + neg1[c] + negA[r][c], a.Kc[c], a.Gc[c]);
+            }
+            *reinterpret_cast<longlong2 *>(y + ur[r] * Dd + d0) = o;
+        }
+    }
+}

@@ -266,23 +266,6 @@ __device__ __forceinline__ I128 block_sum128(I128 v) {
     return r;  // valid in thread 0
 }
 
-// <a, b> with every 128-bit product shifted right by `sh` bits first, so that
-// vectors far from unit norm (a fresh start vector) cannot overflow 128 bits.
-__global__ void k_fx_dot(const int64_t *__restrict__ a, const int64_t *__restrict__ b, uint64_t n, int sh,
-                         I128 *__restrict__ partials) {
-    I128 acc;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const int64_t ph = __mul64hi(a[i], b[i]);
-        const uint64_t pl = (uint64_t)a[i] * (uint64_t)b[i];
-        I128 p;
-        p.lo = sh == 0 ? pl : ((pl >> sh) | ((uint64_t)ph << (64 - sh)));
-        p.hi = sh == 0 ? ph : (ph >> sh);
-        i128_add(acc, p);
-    }
-    const I128 s = block_sum128(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
 __global__ void k_fx_axpy_dot(int64_t *__restrict__ w, const int64_t *__restrict__ vprev,
                               const double *__restrict__ beta_prev, const int64_t *__restrict__ v, uint64_t n,
                               I128 *__restrict__ partials) {
@@ -344,6 +327,18 @@ __global__ void k_fill_random_fx(int64_t *__restrict__ v, uint64_t n, uint64_t s
         const int64_t q = F >= 52 ? (k << (F - 52)) : ((k + (1ll << (51 - F))) >> (52 - F));
         v[i] = q - (1ll << F);
     }
+}
+
+// partial sums of (q 2^-F)^2 in float64: the norm of a fixed-point vector of any
+// scale (a start vector need not be near unit norm), once per solve
+__global__ void k_fx_norm2_f64(const int64_t *__restrict__ v, uint64_t n, int F, double *__restrict__ partials) {
+    double acc = 0.0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const double t = ldexp((double)v[i], -F);
+        acc = fma(t, t, acc);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 __global__ void k_f32_to_fx(const float *__restrict__ a, int64_t *__restrict__ b, uint64_t n, int F) {
@@ -497,11 +492,9 @@ struct Solve {
 template <typename T>
 hb_status normalise(Solve &s, T *v) {
     if constexpr (std::is_same<T, int64_t>::value) {
-        const int nb = s.nblk;
-        I128 *part = reinterpret_cast<I128 *>(s.partials);
-        // |v_i| < 2^62 and up to 2^33 elements: dropping 32 bits per product keeps the sum in 128 bits
-        k_fx_dot<<<nb, kRedThreads, 0, s.st>>>(v, v, s.D, 32, part);
-        k_reduce128<<<1, kFinalThreads, 0, s.st>>>(part, nb, s.d_misc, 1, s.h->fx_frac, 32);
+        // a fresh start vector can be of any scale: its norm is taken in float64 (once per solve)
+        k_fx_norm2_f64<<<s.nblk, kRedThreads, 0, s.st>>>(v, s.D, s.h->fx_frac, s.partials);
+        k_reduce<<<1, kFinalThreads, 0, s.st>>>(s.partials, s.nblk, s.d_misc, 1);
         k_fx_scale<<<s.grid_vec, kRedThreads, 0, s.st>>>(v, s.d_misc, s.D);
     } else {
         k_dot<T><<<s.nblk, kRedThreads, 0, s.st>>>(v, v, s.D, s.partials);

@@ -286,11 +286,11 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
     }
 }
 
-// start vector entries: v = sign * exp(min(out0, 20) - 20)
+// start vector entries: v = sign * exp(min(out0, 10) - 10)
 template <typename T>
 __global__ void k_start_values(const float *__restrict__ out, uint64_t n, T *__restrict__ v, int F) {
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
-        const float a = __expf(fminf(out[2 * r], 20.f) - 20.f);
+        const float a = __expf(fminf(out[2 * r], 10.f) - 10.f);
         const float s = out[2 * r + 1] >= 0.f ? a : -a;
         if constexpr (sizeof(T) == 8 && !std::is_floating_point<T>::value)
             v[r] = (T)__double2ll_rn(ldexp((double)s, F - 1));

@@ -211,3 +211,17 @@ def test_square4x4_fx64_ground_state(env):
     r2 = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0, dtype=torch.float32, fp64_finish="fx64")
     assert r2.converged and close(r2.E0, rec["E0"])
     h.close()
+
+
+@pytest.mark.parametrize("scale_bits", [-40, 0, 8])
+def test_fx64_start_vector_of_any_scale(env, scale_bits):
+    """A fixed-point start vector far from unit norm (tiny or large integers) is normalised correctly."""
+    torch, pd = env
+    cl = wl.ring(8)
+    h = handle_for(cl, 4.0, 4, 4)
+    F = pd.hubbard_fixed_point_bits(h)
+    x = torch.from_numpy(start_vector(3, h.D)).cuda()
+    q = torch.round(x * 2.0 ** (F + scale_bits - 12)).to(torch.int64)  # |q| up to 2^(F+scale-12)
+    r = pd.lanczos_ground_state(h, maxit=400, tol=1e-10, dtype=torch.int64, v0=q)
+    assert r.converged and close(r.E0, golden("ring8_U4_4_4")["E0"])
+    h.close()
