@@ -96,6 +96,22 @@ def ncu_traffic(kernel_key: str):
     return d.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value over all ranks (the job's time is its slowest replica's)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(states_per_replica: int, world: int, ms_per_step: float) -> float:
+    """Whole-job Gstates/s of `world` independent replicas (weak scaling: each does a full step)."""
+    return world * states_per_replica / (ms_per_step * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -218,10 +234,7 @@ def run_ours(args, world, rank, local):
         dist.barrier()
     ms = t_start.elapsed_time(t_end) / args.steps
     hv_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_hv)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, world, dev)
     ab = beta[:nsteps].cpu().numpy()
     sane = bool((ab > 0).all())
 
@@ -242,10 +255,7 @@ def run_ours(args, world, rank, local):
     t1e.record(stream)
     torch.cuda.synchronize()
     e2e_ms = t0e.elapsed_time(t1e) / e2e_steps
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     host_bytes = host_v.element_size()
 
     solve = None
@@ -267,7 +277,7 @@ def run_ours(args, world, rank, local):
     kname = {"f64": "k_hv<2,double,true>", "fx64": "k_hv_fx<2,2,true>", "f32": "k_hv<4,float,true>"}[args.dtype]
     traffic = ncu_traffic(kname)
     out = {
-        "metric": METRIC, "value": round(world * D / (ms * 1e-3) / 1e9, 4), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": round(job_throughput(D, world, ms), 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"f64": "f64", "fx64": "int64", "f32": "f32"}[args.dtype],
@@ -279,7 +289,7 @@ def run_ours(args, world, rank, local):
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "kernel": kname, "bytes_per_state": bps,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
-        "e2e": {"value": round(world * D / (e2e_ms * 1e-3) / 1e9, 4), "unit": UNIT,
+        "e2e": {"value": round(job_throughput(D, world, e2e_ms), 4), "unit": UNIT,
                 "h2d_bytes_per_step": D * host_bytes, "d2h_bytes_per_step": 16},
         "gpu_launches": int(launches.value),
         "clocks": clk,

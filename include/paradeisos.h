@@ -126,8 +126,6 @@ typedef struct {
     int32_t threads_per_cta;  /* multiple of 32, <= 1024 (0 = 1024) */
     int32_t visit_order;      /* 1: rows in reverse Cuthill-McKee order of the spin-up hop graph (default);
                                  0: storage order.  Only the visiting order changes, never the layout. */
-    int32_t column_pairs;     /* HB_FX64 with even D_dn: 1 = two adjacent columns per thread
-                                 (16-byte loads and stores), 0 = one column per thread */
     float ms;                 /* hubbard_autotune: time per H·v of the chosen configuration */
 } hb_hv_config;
 
@@ -136,7 +134,7 @@ hb_status hubbard_get_hv_config(hb_handle h, hb_dtype dt, hb_hv_config *cfg);
  * shared memory falls back to the widest that does. */
 hb_status hubbard_set_hv_config(hb_handle h, hb_dtype dt, const hb_hv_config *cfg);
 /* Autotuner: times every candidate configuration (rows 1/2/4, threads
- * 256/512/1024, both visiting orders, column pairs for HB_FX64) as reps applications of H to the caller's
+ * 256/512/1024, both visiting orders) as reps applications of H to the caller's
  * x (into y, which is overwritten), keeps the fastest in the handle and
  * returns it in *best (may be NULL).  Synchronises `stream`. */
 hb_status hubbard_autotune(hb_handle h, hb_dtype dt, const void *x, void *y, int32_t reps, hb_hv_config *best,

@@ -52,6 +52,12 @@ hb_status mlp_last_error(hb_mlp_handle m);
  * Synchronises `stream`. */
 hb_status mlp_tc_gemm(const void *A, const void *B, float *C, int M, int N, int K, void *stream);
 
+/* Failure-detection self test (synchronous): a kernel waits, with the bounded
+ * mbarrier wait used by the tensor-core kernels, on a barrier that nothing
+ * arrives at; returns HB_ERR_TIMEOUT after max_tries polls (the device stays
+ * usable), HB_OK never (nothing arrives), HB_ERR_CUDA on a runtime error. */
+hb_status hb_device_wait_selftest(uint32_t max_tries);
+
 #ifdef __cplusplus
 }
 #endif

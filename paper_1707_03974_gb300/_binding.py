@@ -33,11 +33,11 @@ class HubbardError(RuntimeError):
 
 class HvConfig(ctypes.Structure):
     _fields_ = [("rows_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("visit_order", ctypes.c_int32), ("column_pairs", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("visit_order", ctypes.c_int32), ("ms", ctypes.c_float)]
 
     def as_dict(self):
         return {"rows_per_cta": self.rows_per_cta, "threads_per_cta": self.threads_per_cta,
-                "visit_order": self.visit_order, "column_pairs": self.column_pairs, "ms": self.ms}
+                "visit_order": self.visit_order, "ms": self.ms}
 
 
 class LanczosOpts(ctypes.Structure):
@@ -90,6 +90,7 @@ def load():
         "mlp_start_vector": (ctypes.c_int, [P, P, I32, P, P]),
         "mlp_last_error": (ctypes.c_int, [P]),
         "mlp_tc_gemm": (ctypes.c_int, [P, P, P, I32, I32, I32, P]),
+        "hb_device_wait_selftest": (ctypes.c_int, [ctypes.c_uint32]),
         "hubbard_batch_create": (ctypes.c_int, [I32, P, ctypes.POINTER(P)]),
         "hubbard_batch_destroy": (ctypes.c_int, [P]),
         "hubbard_batch_layout": (ctypes.c_int, [P, P]),
@@ -240,8 +241,8 @@ def hubbard_get_hv_config(h: "Handle", dtype) -> dict:
     return c.as_dict()
 
 
-def hubbard_set_hv_config(h: "Handle", dtype, rows_per_cta=0, threads_per_cta=0, visit_order=1, column_pairs=0):
-    c = HvConfig(int(rows_per_cta), int(threads_per_cta), int(visit_order), int(column_pairs), 0.0)
+def hubbard_set_hv_config(h: "Handle", dtype, rows_per_cta=0, threads_per_cta=0, visit_order=1):
+    c = HvConfig(int(rows_per_cta), int(threads_per_cta), int(visit_order), 0.0)
     _check(load().hubbard_set_hv_config(h.ptr, _dtype_of(dtype), ctypes.byref(c)), "hubbard_set_hv_config")
 
 
@@ -567,6 +568,10 @@ def mlp_start_vector(m: Mlp, h: Handle, dtype, stream=None):
 
 def mlp_last_error(m: Mlp) -> str:
     return STATUS[load().mlp_last_error(m.ptr)]
+
+
+def hb_device_wait_selftest(max_tries: int = 1000) -> str:
+    return STATUS[load().hb_device_wait_selftest(int(max_tries))]
 
 
 def mlp_tc_gemm(A, B, stream=None):

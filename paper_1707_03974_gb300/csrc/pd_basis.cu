@@ -127,12 +127,11 @@ __global__ void k_spin_hops(const uint32_t *__restrict__ g_lut, const uint32_t *
     }
 }
 
-// The same hops re-ordered for the fixed-point path: grouped by amplitude
-// class (class-major, bond order within a class); each entry is the target
-// index with the fermion sign in bit 31 (set = negative), and seg[r] packs the
-// per-class counts as bytes.  The H·v then adds plain integers per class, the
-// sign folded in as (x XOR m) + (m AND 1), and applies each class's amplitude
-// once per element.
+// The same hops re-ordered for the fixed-point path: segments of equal
+// (amplitude class, fermion sign), class-major, positive sign first; seg[r]
+// packs the 2*PD_FX_MAXC segment lengths as bytes (byte 2c: class c positive,
+// byte 2c+1: class c negative).  The H·v then adds plain 64-bit integers per
+// segment and applies each class's amplitude once per element.
 __global__ void k_spin_hops_fx(const uint32_t *__restrict__ g_lut, const uint32_t *__restrict__ str, uint64_t D,
                                const int32_t *__restrict__ bonds, const int32_t *__restrict__ bond_class,
                                int n_bonds, uint32_t *__restrict__ ftarget, uint64_t *__restrict__ seg) {
@@ -140,16 +139,18 @@ __global__ void k_spin_hops_fx(const uint32_t *__restrict__ g_lut, const uint32_
     load_lut(lut, g_lut);
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < D; r += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t s = str[r];
-        int cnt[PD_FX_MAXC] = {0, 0, 0, 0};
+        int cnt[2 * PD_FX_MAXC] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int b = 0; b < n_bonds; ++b) {
             const int i = bonds[2 * b], j = bonds[2 * b + 1];
             if (((s >> i) & 1u) == ((s >> j) & 1u)) continue;
-            ++cnt[bond_class[b]];
+            const int lo = min(i, j), hi = max(i, j);
+            const uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
+            ++cnt[2 * bond_class[b] + (__popc(s & between) & 1)];
         }
-        int off[PD_FX_MAXC];
+        int off[2 * PD_FX_MAXC];
         uint64_t packed = 0;
         int acc = 0;
-        for (int q = 0; q < PD_FX_MAXC; ++q) {
+        for (int q = 0; q < 2 * PD_FX_MAXC; ++q) {
             off[q] = acc;
             acc += cnt[q];
             packed |= (uint64_t)cnt[q] << (8 * q);
@@ -160,9 +161,8 @@ __global__ void k_spin_hops_fx(const uint32_t *__restrict__ g_lut, const uint32_
             if (((s >> i) & 1u) == ((s >> j) & 1u)) continue;
             const int lo = min(i, j), hi = max(i, j);
             const uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
-            const uint32_t neg = (uint32_t)(__popc(s & between) & 1) << 31;
-            const int q = bond_class[b];
-            ftarget[(uint64_t)(off[q]++) * D + r] = pd_forward_map(lut, s ^ ((1u << i) | (1u << j))) | neg;
+            const int q = 2 * bond_class[b] + (__popc(s & between) & 1);
+            ftarget[(uint64_t)(off[q]++) * D + r] = pd_forward_map(lut, s ^ ((1u << i) | (1u << j)));
         }
     }
 }

@@ -600,7 +600,6 @@ hb_status hubbard_batch_autotune(hb_batch_handle b, hb_dtype dt, const void *x, 
         best->rows_per_cta = bestR;
         best->threads_per_cta = bestT;
         best->visit_order = 1;
-        best->column_pairs = 0;
         best->ms = best_ms;
     }
     return HB_OK;

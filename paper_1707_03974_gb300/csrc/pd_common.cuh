@@ -21,8 +21,6 @@
         if (e_ != cudaSuccess) return HB_ERR_CUDA;      \
     } while (0)
 
-#define PD_TGT_MASK 0x7FFFFFFFu  // target bits of a fixed-point hop entry (bit 31: sign)
-
 // Per-spin tables of one sector: the ascending list of strings (built by the
 // backward map) and the hop lists in ELL layout, entry k of string r at
 // [k * D + r], so that threads handling consecutive strings read consecutive
@@ -37,9 +35,9 @@ struct SpinTables {
     uint32_t *target = nullptr;  // [zmax * D]
     double *val = nullptr;       // [zmax * D]
     float *valf = nullptr;       // [zmax * D] binary32 copy of val
-    // fixed-point path: the same hops grouped by amplitude class,
-    // ftarget[k * D + r] = target | (negative sign << 31); seg[r] packs the
-    // per-class counts as bytes (class c at byte c).
+    // fixed-point path: the same hops in segments of equal (amplitude class,
+    // sign), ftarget[k * D + r]; seg[r] packs the 2*PD_FX_MAXC segment lengths
+    // as bytes (byte 2c: class c positive sign, byte 2c+1: negative).
     uint32_t *ftarget = nullptr;
     uint64_t *seg = nullptr;
 };
@@ -56,7 +54,6 @@ struct HvConfig {
     int rows = 0;     // rows of x staged per CTA group (1, 2 or 4)
     int threads = 0;  // threads per CTA (multiple of 32, <= 1024)
     int order = 1;    // 1: reverse Cuthill-McKee row visiting order, 0: storage order
-    int pair = 0;     // fixed point: two adjacent columns per thread (16-byte accesses)
 };
 
 struct hb_basis {

@@ -107,15 +107,6 @@ __global__ void __launch_bounds__(LB) k_hv_fx(const FxArgs a, const int64_t *__r
     for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) hv_fx_group<R, NC, SMEM>(a, x, y, g, smem);
 }
 
-// two adjacent columns per thread (D_dn even, rows staged in shared memory)
-template <int R, int NC, int LB>
-__global__ void __launch_bounds__(LB) k_hv_fx_pair(const FxArgs a, const int64_t *__restrict__ x,
-                                                   int64_t *__restrict__ y) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    hv_fx_load_diag(a, smem);
-    const uint64_t ngroups = (a.Du + R - 1) / R;
-    for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) hv_fx_group_pair<R, NC>(a, x, y, g, smem);
-}
 
 
 template <int R, int NC, bool SMEM, int LB>
@@ -133,29 +124,8 @@ hb_status launch_hv_fx_lb(hb_handle h, const FxArgs &a, const int64_t *x, int64_
     return HB_OK;
 }
 
-template <int R, int NC, int LB>
-hb_status launch_hv_fx_pair_lb(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st,
-                               int threads) {
-    auto kern = k_hv_fx_pair<R, NC, LB>;
-    const size_t smem = hv_fx_smem_bytes(R, a.zmax_up, a.Dd, true);
-    PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-    if (per_sm < 1) return HB_ERR_NO_MEMORY;
-    const uint64_t ngroups = (a.Du + R - 1) / R;
-    const uint64_t grid = std::min<uint64_t>(ngroups, (uint64_t)per_sm * h->sm_count);
-    kern<<<(unsigned)grid, threads, smem, st>>>(a, x, y);
-    PD_CUDA(cudaGetLastError());
-    return HB_OK;
-}
-
 template <int R, int NC, bool SMEM>
-hb_status launch_hv_fx(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st, int threads,
-                       bool pair) {
-    if (pair && SMEM && a.Dd % 2 == 0) {
-        if (threads <= 512) return launch_hv_fx_pair_lb<R, NC, 512>(h, a, x, y, st, threads);
-        return launch_hv_fx_pair_lb<R, NC, 1024>(h, a, x, y, st, threads);
-    }
+hb_status launch_hv_fx(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st, int threads) {
     if (threads <= 512) return launch_hv_fx_lb<R, NC, SMEM, 512>(h, a, x, y, st, threads);
     return launch_hv_fx_lb<R, NC, SMEM, 1024>(h, a, x, y, st, threads);
 }
@@ -168,10 +138,9 @@ hb_status apply_fx_nc(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y
     int R = cfg.rows;
     if (R != 1 && R != 2) R = 0;
     if (R == 0 || !fits(R)) R = fits(2) ? 2 : fits(1) ? 1 : 0;
-    const bool pair = cfg.pair != 0;
-    if (R == 2) return launch_hv_fx<2, NC, true>(h, a, x, y, st, threads, pair);
-    if (R == 1) return launch_hv_fx<1, NC, true>(h, a, x, y, st, threads, pair);
-    return launch_hv_fx<1, NC, false>(h, a, x, y, st, threads, false);  // rows too long for shared memory
+    if (R == 2) return launch_hv_fx<2, NC, true>(h, a, x, y, st, threads);
+    if (R == 1) return launch_hv_fx<1, NC, true>(h, a, x, y, st, threads);
+    return launch_hv_fx<1, NC, false>(h, a, x, y, st, threads);  // rows too long for shared memory
 }
 
 hb_status apply_fx(hb_handle h, const int64_t *x, int64_t *y, cudaStream_t st) {
@@ -224,7 +193,6 @@ extern "C" hb_status hubbard_get_hv_config(hb_handle h, hb_dtype dt, hb_hv_confi
     cfg->rows_per_cta = c.rows;
     cfg->threads_per_cta = c.threads;
     cfg->visit_order = c.order;
-    cfg->column_pairs = c.pair;
     cfg->ms = 0.f;
     return HB_OK;
 }
@@ -232,14 +200,12 @@ extern "C" hb_status hubbard_get_hv_config(hb_handle h, hb_dtype dt, hb_hv_confi
 extern "C" hb_status hubbard_set_hv_config(hb_handle h, hb_dtype dt, const hb_hv_config *cfg) {
     if (!h || !cfg || (dt != HB_F64 && dt != HB_F32 && dt != HB_FX64)) return HB_ERR_INVALID_ARG;
     if (cfg->rows_per_cta < 0 || cfg->rows_per_cta > 4 || cfg->threads_per_cta < 0 || cfg->threads_per_cta > 1024 ||
-        cfg->threads_per_cta % 32 != 0 || (cfg->visit_order != 0 && cfg->visit_order != 1) ||
-        (cfg->column_pairs != 0 && cfg->column_pairs != 1))
+        cfg->threads_per_cta % 32 != 0 || (cfg->visit_order != 0 && cfg->visit_order != 1))
         return HB_ERR_INVALID_ARG;
     HvConfig &c = h->hv_cfg[dt];
     c.rows = cfg->rows_per_cta;
     c.threads = cfg->threads_per_cta;
     c.order = cfg->visit_order;
-    c.pair = cfg->column_pairs;
     return HB_OK;
 }
 
@@ -265,11 +231,10 @@ extern "C" hb_status hubbard_autotune(hb_handle h, hb_dtype dt, const void *x, v
     const int thr_c[3] = {256, 512, 1024};
     for (int order = 0; order <= 1 && s == HB_OK; ++order)
         for (int ri = 0; ri < (dt == HB_FX64 ? 2 : 3) && s == HB_OK; ++ri)
-            for (int ti = 0; ti < (dt == HB_FX64 ? 6 : 3) && s == HB_OK; ++ti) {
+            for (int ti = 0; ti < 3 && s == HB_OK; ++ti) {
                 HvConfig c;
                 c.rows = rows_c[ri];
-                c.threads = thr_c[ti % 3];
-                c.pair = ti >= 3 ? 1 : 0;
+                c.threads = thr_c[ti];
                 c.order = order;
                 h->hv_cfg[dt] = c;
                 s = pd_apply(h, dt, x, y, st);  // warm-up
@@ -294,7 +259,6 @@ extern "C" hb_status hubbard_autotune(hb_handle h, hb_dtype dt, const void *x, v
         best->rows_per_cta = win.rows;
         best->threads_per_cta = win.threads;
         best->visit_order = win.order;
-        best->column_pairs = win.pair;
         best->ms = win_ms;
     }
     return HB_OK;

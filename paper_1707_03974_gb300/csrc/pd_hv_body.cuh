@@ -26,10 +26,10 @@ struct HvArgs {
     int zmax_up;
 };
 
-// Shared memory of a float group: [up cols R*zmax u32][up vals R*zmax T][up counts R int][x rows R*Dd T]
+// Shared memory of a float group: [up row offsets R*zmax u64][up vals R*zmax T][up counts R int][x rows R*Dd T]
 __host__ __device__ inline size_t hv_smem_bytes(int R, int zmax, size_t tsize, uint64_t Dd, bool smem_rows) {
     const int zr = zmax > 0 ? zmax : 1;
-    size_t off = ((size_t)R * zr * sizeof(uint32_t) + 15) & ~(size_t)15;
+    size_t off = ((size_t)R * zr * sizeof(uint64_t) + 15) & ~(size_t)15;
     off = (off + (size_t)R * zr * tsize + 15) & ~(size_t)15;
     off = (off + R * sizeof(int) + 15) & ~(size_t)15;
     if (smem_rows) off += (size_t)R * Dd * tsize;
@@ -41,9 +41,9 @@ template <int R, typename T, bool SMEM>
 __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict__ x, T *__restrict__ y, uint64_t g,
                                          unsigned char *smem) {
     const uint64_t Dd = a.Dd;
-    uint32_t *s_ucol = reinterpret_cast<uint32_t *>(smem);
+    uint64_t *s_uoff = reinterpret_cast<uint64_t *>(smem);  // spin-up hop rows as element offsets u' * D_dn
     const int zr = a.zmax_up > 0 ? a.zmax_up : 1;
-    size_t off = ((size_t)R * zr * sizeof(uint32_t) + 15) & ~(size_t)15;
+    size_t off = ((size_t)R * zr * sizeof(uint64_t) + 15) & ~(size_t)15;
     T *s_uval = reinterpret_cast<T *>(smem + off);
     off = (off + (size_t)R * zr * sizeof(T) + 15) & ~(size_t)15;
     int *s_nup = reinterpret_cast<int *>(smem + off);
@@ -62,7 +62,7 @@ __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict
         const int r = e / zr, k = e - r * zr;
         if (r < nr && k < a.zmax_up) {
             const uint64_t u = a.order ? (uint64_t)a.order[p0 + r] : p0 + r;
-            s_ucol[e] = a.tgt_up[(uint64_t)k * a.Du + u];
+            s_uoff[e] = (uint64_t)a.tgt_up[(uint64_t)k * a.Du + u] * Dd;
             s_uval[e] = a.val_up[(uint64_t)k * a.Du + u];
         }
     }
@@ -116,7 +116,7 @@ __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict
                 T xv[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    xv[i] = (k0 + i < nu) ? x[(uint64_t)s_ucol[r * zr + k0 + i] * Dd + d] : T(0);
+                    xv[i] = (k0 + i < nu) ? x[s_uoff[r * zr + k0 + i] + d] : T(0);
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     if (k0 + i < nu) acc[r] += s_uval[r * zr + k0 + i] * xv[i];
@@ -129,12 +129,14 @@ __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// Fixed-point (HB_FX64) group.  Hops are grouped per spin string by amplitude
-// class c, each carrying its fermion sign; the group forms the exact integer
-// sums S_c = sum sigma_k x_k (a negative term added as (x XOR -1) + 1), then
-// applies each class's amplitude -t_c once per element:
-//     y = U docc x + sum_c (-t_c) S_c,
-// each product rounded once.  The float64 pipe is never used.
+// Fixed-point (HB_FX64) group.  Hops come in segments of equal amplitude class
+// c and fermion sign; the group forms the exact integer sums P_c (positive
+// sign) and N_c (negative sign) of the 64-bit elements, then applies each
+// class's amplitude -t_c once per element:
+//     y = U docc x + sum_c (-t_c) (P_c - N_c),
+// each product rounded once.  The float64 pipe is never used.  The spin-up
+// hop list is the same for the whole CTA: its row offsets u' * D_dn are staged
+// in shared memory once per group.
 struct FxArgs {
     uint64_t Du, Dd;
     const uint32_t *str_up, *str_dn;
@@ -148,12 +150,12 @@ struct FxArgs {
     int Gd[PD_MAXL + 1];
 };
 
-// Shared memory: [diag K (33 i64)][diag G (33 int)][up seg R u64][up targets R*zr u32][x rows R*Dd i64]
+// Shared memory: [diag K (33 i64)][diag G (33 int)][up seg R u64][up row offsets R*zr u64][x rows R*Dd i64]
 __host__ __device__ inline size_t hv_fx_smem_bytes(int R, int zmax, uint64_t Dd, bool rows = true) {
     const int zr = zmax > 0 ? zmax : 1;
     size_t off = (8 * (PD_MAXL + 1) + 4 * (PD_MAXL + 1) + 15) & ~(size_t)15;
     off = (off + 8 * R + 15) & ~(size_t)15;
-    off = (off + (size_t)R * zr * 4 + 15) & ~(size_t)15;
+    off = (off + (size_t)R * zr * 8 + 15) & ~(size_t)15;
     return off + (rows ? (size_t)R * Dd * 8 : 0);
 }
 
@@ -178,8 +180,8 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
     size_t off = (8 * (PD_MAXL + 1) + 4 * (PD_MAXL + 1) + 15) & ~(size_t)15;
     uint64_t *s_useg = reinterpret_cast<uint64_t *>(smem + off);
     off = (off + 8 * R + 15) & ~(size_t)15;
-    uint32_t *s_ucol = reinterpret_cast<uint32_t *>(smem + off);
-    off = (off + (size_t)R * zr * 4 + 15) & ~(size_t)15;
+    uint64_t *s_uoff = reinterpret_cast<uint64_t *>(smem + off);
+    off = (off + (size_t)R * zr * 8 + 15) & ~(size_t)15;
     int64_t *s_x = reinterpret_cast<int64_t *>(smem + off);
 
     const uint64_t p0 = g * R;
@@ -194,7 +196,7 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
         const int r = e / zr, k = e - r * zr;
         if (r < nr && k < a.zmax_up) {
             const uint64_t u = a.order ? (uint64_t)a.order[p0 + r] : p0 + r;
-            s_ucol[e] = a.ft_up[(uint64_t)k * a.Du + u];
+            s_uoff[e] = (uint64_t)a.ft_up[(uint64_t)k * a.Du + u] * Dd;
         }
     }
     if (SMEM) {
@@ -211,20 +213,17 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
     for (int r = 0; r < R; ++r) su[r] = r < nr ? a.str_up[ur[r]] : 0u;
 
     for (uint64_t d = threadIdx.x; d < Dd; d += blockDim.x) {
-        int64_t acc[R][NC];
-        int negB[NC];
+        int64_t acc[R][2 * NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            negB[c] = 0;
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r][c] = 0;
-        }
+            for (int q = 0; q < 2 * NC; ++q) acc[r][q] = 0;
         // spin-down hops of column d: gathers within the staged rows, table loads in batches of 4
         const uint64_t sg = a.seg_dn[d];
         uint64_t k = 0;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int n = (int)((sg >> (8 * c)) & 0xFFu);
+        for (int q = 0; q < 2 * NC; ++q) {
+            const int n = (int)((sg >> (8 * q)) & 0xFFu);
             for (int i0 = 0; i0 < n; i0 += 4) {
                 uint32_t e[4];
 #pragma unroll
@@ -233,38 +232,28 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
                     if (i0 + i < n) {
-                        const int64_t m = (int64_t)((int32_t)e[i] >> 31);
-                        const uint64_t dk = e[i] & PD_TGT_MASK;
-                        negB[c] += (int)(e[i] >> 31);
 #pragma unroll
                         for (int r = 0; r < R; ++r)
-                            acc[r][c] += (SMEM ? s_x[dk * R + r] : (r < nr ? x[ur[r] * Dd + dk] : 0)) ^ m;
+                            acc[r][q] += SMEM ? s_x[(uint64_t)e[i] * R + r] : (r < nr ? x[ur[r] * Dd + e[i]] : 0);
                     }
             }
             k += n;
         }
         // spin-up hops of row ur[r] (the same list for the whole CTA): 8 loads in flight
-        int negA[R][NC];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint64_t ug = s_useg[r];
+            const uint64_t *uo = s_uoff + r * zr;
             int kk = 0;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                negA[r][c] = 0;
-                const int n = (int)((ug >> (8 * c)) & 0xFFu);
+            for (int q = 0; q < 2 * NC; ++q) {
+                const int n = (int)((ug >> (8 * q)) & 0xFFu);
                 for (int i0 = 0; i0 < n; i0 += 8) {
                     int64_t xv[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        xv[i] = (i0 + i < n) ? x[(uint64_t)(s_ucol[r * zr + kk + i0 + i] & PD_TGT_MASK) * Dd + d] : 0;
+                    for (int i = 0; i < 8; ++i) xv[i] = (i0 + i < n) ? x[uo[kk + i0 + i] + d] : 0;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (i0 + i < n) {
-                            const uint32_t e = s_ucol[r * zr + kk + i0 + i];
-                            acc[r][c] += xv[i] ^ (int64_t)((int32_t)e >> 31);
-                            negA[r][c] += (int)(e >> 31);
-                        }
+                    for (int i = 0; i < 8; ++i) acc[r][q] += xv[i];
                 }
                 kk += n;
             }
@@ -277,150 +266,8 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
             const int64_t xd = SMEM ? s_x[d * R + r] : x[ur[r] * Dd + d];
             int64_t out = fx_mul(xd, s_kd[docc], s_gd[docc]);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) out += fx_mul(acc[r][c] + negB[c] + negA[r][c], a.Kc[c], a.Gc[c]);
+            for (int c = 0; c < NC; ++c) out += fx_mul(acc[r][2 * c] - acc[r][2 * c + 1], a.Kc[c], a.Gc[c]);
             y[ur[r] * Dd + d] = out;
-        }
-    }
-}
-
-// Fixed-point group with two adjacent columns per thread (D_dn even): the
-// staged rows and the spin-up rows are read as 16-byte pairs, and the two
-// columns' spin-down hop lists are walked together, so each thread keeps twice
-// as many independent loads in flight.  Same arithmetic, same results as
-// hv_fx_group (integer sums are exact; the final products are per element).
-template <int R, int NC>
-__device__ __forceinline__ void hv_fx_group_pair(const FxArgs &a, const int64_t *__restrict__ x,
-                                                 int64_t *__restrict__ y, uint64_t g, unsigned char *smem) {
-    const uint64_t Dd = a.Dd;
-    const int zr = a.zmax_up > 0 ? a.zmax_up : 1;
-    const int64_t *s_kd = reinterpret_cast<const int64_t *>(smem);
-    const int *s_gd = reinterpret_cast<const int *>(smem + 8 * (PD_MAXL + 1));
-    size_t off = (8 * (PD_MAXL + 1) + 4 * (PD_MAXL + 1) + 15) & ~(size_t)15;
-    uint64_t *s_useg = reinterpret_cast<uint64_t *>(smem + off);
-    off = (off + 8 * R + 15) & ~(size_t)15;
-    uint32_t *s_ucol = reinterpret_cast<uint32_t *>(smem + off);
-    off = (off + (size_t)R * zr * 4 + 15) & ~(size_t)15;
-    int64_t *s_x = reinterpret_cast<int64_t *>(smem + off);
-
-    const uint64_t p0 = g * R;
-    const uint64_t left = a.Du - p0;
-    const int nr = left < (uint64_t)R ? (int)left : R;
-    uint64_t ur[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) ur[r] = r < nr ? (a.order ? (uint64_t)a.order[p0 + r] : p0 + r) : 0;
-    __syncthreads();
-    if (threadIdx.x < R) s_useg[threadIdx.x] = threadIdx.x < nr ? a.seg_up[ur[threadIdx.x]] : 0ull;
-    for (int e = threadIdx.x; e < R * zr; e += blockDim.x) {
-        const int r = e / zr, k = e - r * zr;
-        if (r < nr && k < a.zmax_up) {
-            const uint64_t u = a.order ? (uint64_t)a.order[p0 + r] : p0 + r;
-            s_ucol[e] = a.ft_up[(uint64_t)k * a.Du + u];
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (r >= nr) break;
-        const longlong2 *xr = reinterpret_cast<const longlong2 *>(x + ur[r] * Dd);
-        for (uint64_t p = threadIdx.x; p < Dd / 2; p += blockDim.x) {
-            const longlong2 v = xr[p];
-            s_x[(2 * p) * R + r] = v.x;
-            s_x[(2 * p + 1) * R + r] = v.y;
-        }
-    }
-    __syncthreads();
-    uint32_t su[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) su[r] = r < nr ? a.str_up[ur[r]] : 0u;
-
-    for (uint64_t p = threadIdx.x; p < Dd / 2; p += blockDim.x) {
-        const uint64_t d0 = 2 * p;
-        int64_t acc0[R][NC], acc1[R][NC];
-        int neg0[NC], neg1[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            neg0[c] = neg1[c] = 0;
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc0[r][c] = acc1[r][c] = 0;
-        }
-        // spin-down hops of columns d0 and d0+1, walked together
-        const uint64_t sg0 = a.seg_dn[d0], sg1 = a.seg_dn[d0 + 1];
-        uint64_t k0 = 0, k1 = 0;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int n0 = (int)((sg0 >> (8 * c)) & 0xFFu), n1 = (int)((sg1 >> (8 * c)) & 0xFFu);
-            const int nmax = n0 > n1 ? n0 : n1;
-            for (int i0 = 0; i0 < nmax; i0 += 2) {
-                uint32_t e0[2], e1[2];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    if (i0 + i < n0) e0[i] = a.ft_dn[(k0 + i0 + i) * Dd + d0];
-                    if (i0 + i < n1) e1[i] = a.ft_dn[(k1 + i0 + i) * Dd + d0 + 1];
-                }
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    if (i0 + i < n0) {
-                        const int64_t m = (int64_t)((int32_t)e0[i] >> 31);
-                        const uint64_t dk = e0[i] & PD_TGT_MASK;
-                        neg0[c] += (int)(e0[i] >> 31);
-#pragma unroll
-                        for (int r = 0; r < R; ++r) acc0[r][c] += s_x[dk * R + r] ^ m;
-                    }
-                    if (i0 + i < n1) {
-                        const int64_t m = (int64_t)((int32_t)e1[i] >> 31);
-                        const uint64_t dk = e1[i] & PD_TGT_MASK;
-                        neg1[c] += (int)(e1[i] >> 31);
-#pragma unroll
-                        for (int r = 0; r < R; ++r) acc1[r][c] += s_x[dk * R + r] ^ m;
-                    }
-                }
-            }
-            k0 += n0;
-            k1 += n1;
-        }
-        // spin-up hops: 16-byte column pairs of the rows x[u', :]
-        int negA[R][NC];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint64_t ug = s_useg[r];
-            int kk = 0;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                negA[r][c] = 0;
-                const int n = (int)((ug >> (8 * c)) & 0xFFu);
-                for (int i0 = 0; i0 < n; i0 += 4) {
-                    longlong2 xv[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (i0 + i < n)
-                            xv[i] = *reinterpret_cast<const longlong2 *>(
-                                x + (uint64_t)(s_ucol[r * zr + kk + i0 + i] & PD_TGT_MASK) * Dd + d0);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (i0 + i < n) {
-                            const uint32_t e = s_ucol[r * zr + kk + i0 + i];
-                            const int64_t m = (int64_t)((int32_t)e >> 31);
-                            acc0[r][c] += xv[i].x ^ m;
-                            acc1[r][c] += xv[i].y ^ m;
-                            negA[r][c] += (int)(e >> 31);
-                        }
-                }
-                kk += n;
-            }
-        }
-        const uint32_t sd0 = a.str_dn[d0], sd1 = a.str_dn[d0 + 1];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (r >= nr) continue;
-            const int dc0 = __popc(su[r] & sd0), dc1 = __popc(su[r] & sd1);
-            longlong2 o;
-            o.x = fx_mul(s_x[d0 * R + r], s_kd[dc0], s_gd[dc0]);
-            o.y = fx_mul(s_x[(d0 + 1) * R + r], s_kd[dc1], s_gd[dc1]);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                o.x += fx_mul(acc0[r][c] + neg0[c] + negA[r][c], a.Kc[c], a.Gc[c]);
-                o.y += fx_mul(acc1[r][c] + neg1[c] + negA[r][c], a.Kc[c], a.Gc[c]);
-            }
-            *reinterpret_cast<longlong2 *>(y + ur[r] * Dd + d0) = o;
         }
     }
 }

@@ -95,7 +95,13 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const __nv_bfloat16 *__restrict
         any = true;
         tc::fence_after_sync();
     }
-    if (!ok && tid == 0) atomicOr(err, PD_ERRBIT(HB_ERR_TIMEOUT));
+    if (!ok) {
+        // gave up waiting: record it, then drain (bounded) so no MMA still writes the
+        // tensor memory released below
+        if (tid == 0) atomicOr(err, PD_ERRBIT(HB_ERR_TIMEOUT));
+        tc::mbar_wait(&bar, phase ^ 1, kWaitTries);
+        __syncthreads();
+    }
     if (ok && any) {
         const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
@@ -560,6 +566,28 @@ hb_status mlp_last_error(hb_mlp_handle m) {
     for (int s = 1; s <= (int)HB_ERR_TIMEOUT; ++s)
         if (bits & PD_ERRBIT(s)) return (hb_status)s;
     return HB_OK;
+}
+
+// Failure-detection self test: one CTA waits, with the same bounded mbarrier
+// wait the tensor-core kernels use, on a barrier that nothing arrives at; the
+// wait gives up after max_tries polls and the kernel reports HB_ERR_TIMEOUT
+// through the status word instead of hanging.
+__global__ void k_wait_selftest(uint32_t max_tries, unsigned *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    __syncthreads();
+    const bool ok = tc::mbar_wait(&bar, 0, max_tries);
+    if (threadIdx.x == 0) *status = ok ? 0u : (unsigned)HB_ERR_TIMEOUT;
+}
+
+hb_status hb_device_wait_selftest(uint32_t max_tries) {
+    unsigned *d = nullptr, h = 0;
+    PD_CUDA(cudaMalloc(&d, sizeof(unsigned)));
+    k_wait_selftest<<<1, 32>>>(max_tries, d);
+    cudaError_t e = cudaMemcpy(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return HB_ERR_CUDA;
+    return (hb_status)h;
 }
 
 // C[M, N] = A[M, K] B[N, K]^T on the tensor cores (bf16 in, f32 out), exposed for tests.

@@ -225,3 +225,26 @@ def test_fx64_start_vector_of_any_scale(env, scale_bits):
     r = pd.lanczos_ground_state(h, maxit=400, tol=1e-10, dtype=torch.int64, v0=q)
     assert r.converged and close(r.E0, golden("ring8_U4_4_4")["E0"])
     h.close()
+
+
+def test_nan_start_vector_is_reported(env):
+    """A non-finite start vector ends the solve with an error status instead of a wrong E0."""
+    torch, pd = env
+    h = handle_for(wl.ring(8), 4.0, 4, 4)
+    v0 = torch.from_numpy(start_vector(1, h.D)).cuda()
+    v0[17] = float("nan")
+    with pytest.raises(pd.HubbardError) as e:
+        pd.lanczos_ground_state(h, maxit=50, tol=1e-10, v0=v0)
+    assert e.value.name == "HB_ERR_INVALID_STATE"
+    # the handle and the device stay usable
+    r = pd.lanczos_ground_state(h, maxit=400, tol=1e-10)
+    assert r.converged
+    h.close()
+
+
+def test_bounded_device_wait_reports_timeout(env):
+    """A device wait on a barrier nothing arrives at gives up and reports HB_ERR_TIMEOUT."""
+    torch, pd = env
+    assert pd.hb_device_wait_selftest(2000) == "HB_ERR_TIMEOUT"
+    x = torch.ones(4, device="cuda")
+    assert float(x.sum().item()) == 4.0  # the context is still usable
