@@ -85,6 +85,18 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def hv_kernel_key(dtype: str, cfg: dict) -> str:
+    """Name of the H·v launch(es) under a configuration: one fused kernel, or the row pass
+    followed by the column-blocked spin-up pass (their DRAM bytes are summed)."""
+    rows = cfg.get("rows_per_cta") or {"f64": 2, "fx64": 2, "f32": 4}[dtype]
+    base = {"f64": f"k_hv<{rows},double", "fx64": f"k_hv_fx<{rows},2", "f32": f"k_hv<{rows},float"}[dtype]
+    if not cfg.get("split"):
+        return base + ",true>"
+    up = {"f64": "k_hv_up<{r},double>", "fx64": "k_hv_fx_up<{r},2>", "f32": "k_hv_up<{r},float>"}[dtype]
+    return (f"{base},true,row pass> + " + up.format(r=cfg.get("up_rows") or 1)
+            + f" (block {cfg.get('up_block') or 256}, {cfg.get('up_threads') or 1024} threads)")
+
+
 def ncu_traffic(kernel_key: str):
     """DRAM bytes per launch of the H·v kernel from the committed ncu summary, if it matches this source."""
     p = os.path.join(ROOT, "profiles", "hv_dram_traffic.json")
@@ -310,9 +322,7 @@ def run_ours(args, world, rank, local):
     peak = peaks.get("hbm_gbs") if peaks else 6800.0
     bps = HV_BYTES_PER_STATE if args.dtype != "f32" else 8
     achieved = bps * D / (hv_ms * 1e-3) / 1e9
-    rows = tuned.get("rows_per_cta") or {"f64": 2, "fx64": 2, "f32": 4}[args.dtype]
-    kname = {"f64": f"k_hv<{rows},double,true>", "fx64": f"k_hv_fx<{rows},2,true>",
-             "f32": f"k_hv<{rows},float,true>"}[args.dtype]
+    kname = hv_kernel_key(args.dtype, tuned)
     traffic = ncu_traffic(kname)
     out = {
         "metric": METRIC, "value": round(job_throughput(D, world, ms), 4), "unit": UNIT, "n_gpus": world,

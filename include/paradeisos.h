@@ -115,8 +115,10 @@ hb_status paradeisos_unrank(hb_handle h, const uint64_t *idx, uint64_t *states, 
 /*
  * y = H x, matrix-free (Eq. 1): diagonal U * popcount(up & dn) (Sec. II B) plus
  * every hop of both spins, each target located by the forward map.
- * dt      HB_F64 or HB_F32: element type of x and y (length D each).
+ * dt      HB_F64, HB_F32 or HB_FX64 (fixed point, see hubbard_fixed_point_bits):
+ *         element type of x and y (length D each).
  * x, y    device vectors; must not overlap (HB_ERR_INVALID_ARG).
+ * Every launch configuration (hb_hv_config) gives bit-identical results.
  */
 hb_status hubbard_apply(hb_handle h, hb_dtype dt, const void *x, void *y, void *stream);
 
@@ -127,6 +129,12 @@ typedef struct {
     int32_t visit_order;      /* 1: rows in reverse Cuthill-McKee order of the spin-up hop graph (default);
                                  0: storage order.  Only the visiting order changes, never the layout. */
     float ms;                 /* hubbard_autotune: time per H·v of the chosen configuration */
+    int32_t split;            /* 0: one kernel for all terms; 1: a row pass (diagonal + spin-down hops, the
+                                 fields above) then a spin-up pass over column blocks of x, so the blocks
+                                 in flight stay in L2 (the fields below) */
+    int32_t up_block;         /* split: columns per block, multiple of 32, <= up_threads (0 = 256) */
+    int32_t up_threads;       /* split: threads per CTA, a multiple of up_block, <= 1024 (0 = 1024) */
+    int32_t up_rows;          /* split: rows per thread, 1, 2 or 4 (0 = 1) */
 } hb_hv_config;
 
 hb_status hubbard_get_hv_config(hb_handle h, hb_dtype dt, hb_hv_config *cfg);
@@ -134,9 +142,12 @@ hb_status hubbard_get_hv_config(hb_handle h, hb_dtype dt, hb_hv_config *cfg);
  * shared memory falls back to the widest that does. */
 hb_status hubbard_set_hv_config(hb_handle h, hb_dtype dt, const hb_hv_config *cfg);
 /* Autotuner: times every candidate configuration (rows 1/2/4, threads
- * 256/512/1024, both visiting orders) as reps applications of H to the caller's
- * x (into y, which is overwritten), keeps the fastest in the handle and
- * returns it in *best (may be NULL).  Synchronises `stream`. */
+ * 256/512/1024, both visiting orders, one kernel or split; for the split form
+ * the row pass and the spin-up pass (blocks 128/256/512, threads 512/1024,
+ * rows 1/2/4) are tuned one after the other) as reps applications to the
+ * caller's x (into y, which is overwritten and left unspecified), keeps the
+ * fastest in the handle and returns it in *best (may be NULL).  Synchronises
+ * `stream`. */
 hb_status hubbard_autotune(hb_handle h, hb_dtype dt, const void *x, void *y, int32_t reps, hb_hv_config *best,
                            void *stream);
 

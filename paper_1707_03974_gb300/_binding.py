@@ -33,11 +33,13 @@ class HubbardError(RuntimeError):
 
 class HvConfig(ctypes.Structure):
     _fields_ = [("rows_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("visit_order", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("visit_order", ctypes.c_int32), ("ms", ctypes.c_float), ("split", ctypes.c_int32),
+                ("up_block", ctypes.c_int32), ("up_threads", ctypes.c_int32), ("up_rows", ctypes.c_int32)]
 
     def as_dict(self):
         return {"rows_per_cta": self.rows_per_cta, "threads_per_cta": self.threads_per_cta,
-                "visit_order": self.visit_order, "ms": self.ms}
+                "visit_order": self.visit_order, "ms": self.ms, "split": self.split, "up_block": self.up_block,
+                "up_threads": self.up_threads, "up_rows": self.up_rows}
 
 
 class LanczosOpts(ctypes.Structure):
@@ -241,8 +243,10 @@ def hubbard_get_hv_config(h: "Handle", dtype) -> dict:
     return c.as_dict()
 
 
-def hubbard_set_hv_config(h: "Handle", dtype, rows_per_cta=0, threads_per_cta=0, visit_order=1):
-    c = HvConfig(int(rows_per_cta), int(threads_per_cta), int(visit_order), 0.0)
+def hubbard_set_hv_config(h: "Handle", dtype, rows_per_cta=0, threads_per_cta=0, visit_order=1, split=0,
+                          up_block=0, up_threads=0, up_rows=0, ms=None):
+    c = HvConfig(int(rows_per_cta), int(threads_per_cta), int(visit_order), 0.0, int(split), int(up_block),
+                 int(up_threads), int(up_rows))
     _check(load().hubbard_set_hv_config(h.ptr, _dtype_of(dtype), ctypes.byref(c)), "hubbard_set_hv_config")
 
 

@@ -249,7 +249,152 @@ void free_spin(SpinTables &s) {
     cudaFree(s.valf);
     cudaFree(s.ftarget);
     cudaFree(s.seg);
+    cudaFree(s.wb_perm);
+    cudaFree(s.wb_str);
+    cudaFree(s.wb_base);
+    cudaFree(s.wb_ent);
+    cudaFree(s.wb_caps);
     s = SpinTables();
+}
+
+// Shared-memory bank groups: the row pass reads 16-byte elements (two staged
+// rows), served 8 lanes (one quarter warp) at a time over 8 groups of 4 banks;
+// targets t and t' of one quarter warp in one slot conflict when t = t' mod 8
+// and t != t'.  Local search per quarter warp: swap two slots of one lane when
+// that lowers the summed worst-group load of the two slots.  The sums are
+// exact integer sums, so the order of a lane's hops within a segment is free.
+void balance_banks(std::vector<int32_t> &grid, int slots) {
+    if (slots < 2) return;
+    for (int qw = 0; qw < 4; ++qw) {
+        std::vector<int> cnt((size_t)slots * 8, 0);
+        auto at = [&](int l, int s) -> int32_t & { return grid[(size_t)l * slots + s]; };
+        for (int l = 8 * qw; l < 8 * qw + 8; ++l)
+            for (int s = 0; s < slots; ++s)
+                if (at(l, s) >= 0) ++cnt[(size_t)s * 8 + at(l, s) % 8];
+        auto worst = [&](int s) {
+            int m = 0;
+            for (int g = 0; g < 8; ++g) m = std::max(m, cnt[(size_t)s * 8 + g]);
+            return m;
+        };
+        for (int pass = 0; pass < 4; ++pass) {
+            bool improved = false;
+            for (int l = 8 * qw; l < 8 * qw + 8; ++l)
+                for (int s1 = 0; s1 < slots; ++s1)
+                    for (int s2 = s1 + 1; s2 < slots; ++s2) {
+                        const int32_t a = at(l, s1), b = at(l, s2);
+                        if (a == b) continue;
+                        const int before = worst(s1) + worst(s2);
+                        if (a >= 0) --cnt[(size_t)s1 * 8 + a % 8], ++cnt[(size_t)s2 * 8 + a % 8];
+                        if (b >= 0) --cnt[(size_t)s2 * 8 + b % 8], ++cnt[(size_t)s1 * 8 + b % 8];
+                        if (worst(s1) + worst(s2) < before) {
+                            std::swap(at(l, s1), at(l, s2));
+                            improved = true;
+                        } else {
+                            if (a >= 0) ++cnt[(size_t)s1 * 8 + a % 8], --cnt[(size_t)s2 * 8 + a % 8];
+                            if (b >= 0) ++cnt[(size_t)s2 * 8 + b % 8], --cnt[(size_t)s1 * 8 + b % 8];
+                        }
+                    }
+            if (!improved) break;
+        }
+    }
+}
+
+// Warp-blocked hop table (see SpinTables): built on the host from the
+// segment-ordered fixed-point hop lists.
+hb_status build_wb(SpinTables &st) {
+    const uint64_t D = st.D;
+    if (D == 0 || D + 8 > 65535 || !st.ftarget) return HB_OK;
+    const uint32_t kZeroSlot = 0xFFFFu;  // placeholder until the bank group is chosen
+    const int z = st.zmax > 0 ? st.zmax : 1;
+    std::vector<uint32_t> ft((uint64_t)z * D), str(D);
+    std::vector<uint64_t> seg(D);
+    PD_CUDA(cudaMemcpy(ft.data(), st.ftarget, ft.size() * 4, cudaMemcpyDeviceToHost));
+    PD_CUDA(cudaMemcpy(seg.data(), st.seg, D * 8, cudaMemcpyDeviceToHost));
+    PD_CUDA(cudaMemcpy(str.data(), st.str, D * 4, cudaMemcpyDeviceToHost));
+    constexpr int NQ = 2 * PD_FX_MAXC;
+    auto cnt = [&](uint64_t r, int q) { return (int)((seg[r] >> (8 * q)) & 0xFFu); };
+    std::vector<uint32_t> perm(D);
+    for (uint64_t r = 0; r < D; ++r) perm[r] = (uint32_t)r;
+    std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) {
+        for (int q = 0; q < NQ; ++q)
+            if (cnt(a, q) != cnt(b, q)) return cnt(a, q) < cnt(b, q);
+        return false;
+    });
+    const uint64_t nblk = (D + 31) / 32;
+    std::vector<uint32_t> wperm(nblk * 32, (uint32_t)D), wstr(nblk * 32, 0u), base(nblk);
+    std::vector<uint64_t> caps(nblk, 0ull);
+    std::vector<uint32_t> ent;
+    uint64_t rows = 0;
+    for (uint64_t b = 0; b < nblk; ++b) {
+        int cap[NQ] = {0};
+        for (int l = 0; l < 32; ++l) {
+            const uint64_t p = b * 32 + l;
+            if (p >= D) break;
+            wperm[p] = perm[p];
+            wstr[p] = str[perm[p]];
+            for (int q = 0; q < NQ; ++q) cap[q] = std::max(cap[q], cnt(perm[p], q));
+        }
+        base[b] = (uint32_t)rows;
+        for (int q = 0; q < NQ; ++q) {
+            const int pairs = (cap[q] + 1) / 2, slots = 2 * pairs;
+            caps[b] |= (uint64_t)pairs << (8 * q);
+            // grid[l][s]: target of lane l in slot s (-1: empty)
+            std::vector<int32_t> grid((size_t)32 * slots, -1);
+            for (int l = 0; l < 32; ++l) {
+                const uint64_t p = b * 32 + l;
+                if (p >= D) break;
+                const uint32_t r = perm[p];
+                int k0 = 0;
+                for (int qq = 0; qq < q; ++qq) k0 += cnt(r, qq);
+                for (int i = 0; i < cnt(r, q); ++i) grid[(size_t)l * slots + i] = (int32_t)ft[(uint64_t)(k0 + i) * D + r];
+            }
+            balance_banks(grid, slots);
+            for (int s = 0; s < pairs; ++s, ++rows)
+                for (int l = 0; l < 32; ++l) {
+                    uint32_t t[2];
+                    for (int h = 0; h < 2; ++h) {
+                        const int32_t v = grid[(size_t)l * slots + 2 * s + h];
+                        t[h] = v >= 0 ? (uint32_t)v : kZeroSlot;
+                    }
+                    ent.push_back(t[0] | (t[1] << 16));
+                }
+        }
+    }
+    // empty slots read one of the eight zero elements s_x[D .. D+7]: the one in
+    // the bank group that no real target of the lane's quarter warp uses
+    for (uint64_t b = 0, row = 0; b < nblk; ++b)
+        for (int q = 0; q < NQ; ++q)
+            for (uint64_t pr = 0; pr < ((caps[b] >> (8 * q)) & 0xFFu); ++pr, ++row)
+                for (int h = 0; h < 2; ++h)
+                    for (int qw = 0; qw < 4; ++qw) {
+                        bool used[8] = {false};
+                        for (int l = 8 * qw; l < 8 * qw + 8; ++l) {
+                            const uint32_t t = (ent[row * 32 + l] >> (16 * h)) & 0xFFFFu;
+                            if (t != kZeroSlot) used[t % 8] = true;
+                        }
+                        int z = 0;
+                        while (z < 7 && used[z]) ++z;
+                        const uint32_t zt = (uint32_t)D + (uint32_t)((z - (int)(D % 8) + 8) % 8);
+                        for (int l = 8 * qw; l < 8 * qw + 8; ++l) {
+                            uint32_t &e = ent[row * 32 + l];
+                            if (((e >> (16 * h)) & 0xFFFFu) == kZeroSlot)
+                                e = (e & ~(0xFFFFu << (16 * h))) | (zt << (16 * h));
+                        }
+                    }
+    if (rows >= (1ull << 32) / 32) return HB_OK;
+    PD_CUDA(cudaMalloc(&st.wb_perm, wperm.size() * 4));
+    PD_CUDA(cudaMalloc(&st.wb_str, wstr.size() * 4));
+    PD_CUDA(cudaMalloc(&st.wb_base, base.size() * 4));
+    PD_CUDA(cudaMalloc(&st.wb_caps, caps.size() * 8));
+    PD_CUDA(cudaMalloc(&st.wb_ent, std::max<size_t>(ent.size(), 1) * 4));
+    PD_CUDA(cudaMemcpy(st.wb_perm, wperm.data(), wperm.size() * 4, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(st.wb_str, wstr.data(), wstr.size() * 4, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(st.wb_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(st.wb_caps, caps.data(), caps.size() * 8, cudaMemcpyHostToDevice));
+    if (!ent.empty()) PD_CUDA(cudaMemcpy(st.wb_ent, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice));
+    st.wb_nblk = (uint32_t)nblk;
+    st.wb_ok = true;
+    return HB_OK;
 }
 
 hb_status build_spin(hb_handle h, SpinTables &st, int n) {
@@ -284,6 +429,7 @@ hb_status build_spin(hb_handle h, SpinTables &st, int n) {
         PD_CUDA(cudaGetLastError());
     }
     PD_CUDA(cudaDeviceSynchronize());
+    if (h->fx_ok) return build_wb(st);
     return HB_OK;
 }
 

@@ -601,6 +601,8 @@ hb_status hubbard_batch_autotune(hb_batch_handle b, hb_dtype dt, const void *x, 
         best->threads_per_cta = bestT;
         best->visit_order = 1;
         best->ms = best_ms;
+        best->split = 0;  // the batched H·v is always one kernel
+        best->up_block = best->up_threads = best->up_rows = 0;
     }
     return HB_OK;
 }

@@ -40,6 +40,19 @@ struct SpinTables {
     // as bytes (byte 2c: class c positive sign, byte 2c+1: negative).
     uint32_t *ftarget = nullptr;
     uint64_t *seg = nullptr;
+    // warp-blocked copy of the fixed-point hops for the row pass (built when
+    // D + 8 < 65536): positions p are the strings sorted by their segment
+    // lengths, so the 32 lanes of a warp (one block of 32 positions) share slot
+    // counts.  wb_perm[p]: string at position p (D for padding); wb_str[p]: its
+    // bits; wb_caps[b]: pairs of slots per segment of block b (byte q);
+    // wb_base[b]: first pair row of block b in wb_ent; wb_ent[(pair row) * 32 +
+    // lane]: two u16 targets (lo: even slot, hi: odd slot), D .. D+7 (a zero
+    // element) for an empty slot; slots are ordered to spread each quarter
+    // warp's targets over the shared-memory bank groups.
+    bool wb_ok = false;
+    uint32_t wb_nblk = 0;
+    uint32_t *wb_perm = nullptr, *wb_str = nullptr, *wb_base = nullptr, *wb_ent = nullptr;
+    uint64_t *wb_caps = nullptr;
 };
 
 // A real multiplier c in fixed point: c ~ K * 2^-G with |K| < 2^62, 1 <= G <= 63.
@@ -54,6 +67,10 @@ struct HvConfig {
     int rows = 0;     // rows of x staged per CTA group (1, 2 or 4)
     int threads = 0;  // threads per CTA (multiple of 32, <= 1024)
     int order = 1;    // 1: reverse Cuthill-McKee row visiting order, 0: storage order
+    int split = 0;    // 1: row pass (diagonal + spin-down) then the column-blocked spin-up pass
+    int up_block = 0;    // spin-up pass: columns per block (multiple of 32; 0 = 256)
+    int up_threads = 0;  // spin-up pass: threads per CTA (multiple of up_block, <= 1024; 0 = 1024)
+    int up_rows = 0;     // spin-up pass: rows per thread, 1, 2 or 4 (0 = 1)
 };
 
 struct hb_basis {

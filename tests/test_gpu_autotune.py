@@ -25,6 +25,32 @@ def test_all_configs_bit_identical(dtype_name):
                 pd.hubbard_set_hv_config(h, dtype, rows, threads, order)
                 y = pd.hubbard_apply(h, x).cpu()
                 assert torch.equal(y, ref), (rows, threads, order)
+    # split form: row pass then the column-blocked spin-up pass; D_dn = 126 leaves
+    # ragged column blocks for every block width
+    for rows, threads in ((1, 256), (2, 1024)):
+        for ub, ut in ((32, 64), (64, 512), (128, 1024), (256, 256)):
+            for rr in (1, 2, 4):
+                pd.hubbard_set_hv_config(h, dtype, rows, threads, 1, split=1, up_block=ub, up_threads=ut, up_rows=rr)
+                y = pd.hubbard_apply(h, x).cpu()
+                assert torch.equal(y, ref), (rows, threads, ub, ut, rr)
+    h.close()
+
+
+@pytest.mark.parametrize("dtype_name", ["float64", "float32", "int64"])
+def test_split_matches_fused_on_long_rows(dtype_name):
+    """18 sites, N_up = 1, N_dn = 9: rows of 48,620 elements (too long for shared memory
+    in 8-byte formats), so the row pass gathers from global memory."""
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    dtype = getattr(torch, dtype_name)
+    h = handle_for(wl.ring(18), 4.0, 1, 9)
+    x = torch.from_numpy(start_vector(5, h.D)).cuda()
+    x = pd.hubbard_convert(h, x / x.abs().max(), torch.int64) if dtype_name == "int64" else x.to(dtype)
+    pd.hubbard_set_hv_config(h, dtype, 0, 0, 1)
+    ref = pd.hubbard_apply(h, x).cpu()
+    for ub, ut, rr in ((128, 1024, 1), (256, 512, 2), (512, 1024, 4)):
+        pd.hubbard_set_hv_config(h, dtype, 0, 0, 1, split=1, up_block=ub, up_threads=ut, up_rows=rr)
+        assert torch.equal(pd.hubbard_apply(h, x).cpu(), ref), (ub, ut, rr)
     h.close()
 
 
@@ -37,10 +63,15 @@ def test_autotune_keeps_fastest_and_results_unchanged():
     y = torch.empty_like(x)
     best = pd.hubbard_autotune(h, x, y, reps=2)
     assert best["ms"] > 0 and best["rows_per_cta"] in (1, 2, 4) and best["threads_per_cta"] in (256, 512, 1024)
+    assert best["split"] in (0, 1)
     cur = pd.hubbard_get_hv_config(h, torch.float64)
-    assert (cur["rows_per_cta"], cur["threads_per_cta"], cur["visit_order"]) == \
-        (best["rows_per_cta"], best["threads_per_cta"], best["visit_order"])
+    keys = ("rows_per_cta", "threads_per_cta", "visit_order", "split", "up_block", "up_threads", "up_rows")
+    assert all(cur[k] == best[k] for k in keys)
     assert torch.equal(pd.hubbard_apply(h, x), ref)
     with pytest.raises(pd.HubbardError):
         pd.hubbard_set_hv_config(h, torch.float64, 3, 100, 0)
+    with pytest.raises(pd.HubbardError):  # block wider than the CTA
+        pd.hubbard_set_hv_config(h, torch.float64, 0, 0, 1, split=1, up_block=512, up_threads=256)
+    with pytest.raises(pd.HubbardError):
+        pd.hubbard_set_hv_config(h, torch.float64, 0, 0, 1, split=1, up_rows=3)
     h.close()
