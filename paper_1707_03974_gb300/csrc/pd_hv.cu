@@ -32,14 +32,14 @@ __global__ void __launch_bounds__(LB) k_hv(const HvArgs<T> a, const T *__restric
     for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) hv_group<R, T, SMEM, DO_A>(a, x, y, g, smem);
 }
 
-template <int RR, typename T, bool IDX32, int LB>
+template <int RR, typename T, bool IDX32, int LB, int V>
 __global__ void __launch_bounds__(LB) k_hv_up(const HvArgs<T> a, const T *__restrict__ x, T *__restrict__ y, int W,
                                                 uint64_t n_groups, uint64_t n_items) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = blockDim.x / W;
     ItemWalk w(n_groups);
     for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x, w.next())
-        hv_up_item<RR, T, IDX32>(a, x, y, w.j, w.g, W, S, smem);
+        hv_up_item<RR, T, IDX32, V>(a, x, y, w.j, w.g, W, S, smem);
 }
 
 bool a_small(uint64_t Dd, int threads) { return Dd < (uint64_t)threads; }
@@ -95,18 +95,31 @@ hb_status launch_hv(hb_handle h, const HvArgs<T> &a, const T *x, T *y, cudaStrea
     return launch_hv_lb<R, T, SMEM, 1024, DO_A>(h, a, x, y, st, smem, threads);
 }
 
-template <int RR, typename T, bool IDX32>
-hb_status launch_up(hb_handle h, const HvArgs<T> &a, const T *x, T *y, cudaStream_t st, const UpShape &u) {
+// Two adjacent columns per thread (one vector load per operand) when every row
+// of x and y starts on a 2-element boundary.
+template <typename T>
+bool up_pairs(uint64_t Dd, const void *x, const void *y) {
+    return Dd % 2 == 0 && ((uintptr_t)x | (uintptr_t)y) % (2 * sizeof(T)) == 0;
+}
+
+template <int RR, typename T, bool IDX32, int V>
+hb_status launch_up_v(hb_handle h, const HvArgs<T> &a, const T *x, T *y, cudaStream_t st, const UpShape &u) {
     const int RA = u.S * RR, threads = u.W * u.S;
     const size_t smem = hv_up_smem_bytes<IDX32>(RA, a.zmax_up, sizeof(T));
-    const uint64_t n_groups = (a.Du + RA - 1) / RA, n_items = (a.Dd + u.W - 1) / u.W * n_groups;
-    auto kern = threads <= 512 ? k_hv_up<RR, T, IDX32, 512> : k_hv_up<RR, T, IDX32, 1024>;
+    const uint64_t n_groups = (a.Du + RA - 1) / RA, n_items = (a.Dd + (uint64_t)u.W * V - 1) / ((uint64_t)u.W * V) * n_groups;
+    auto kern = threads <= 512 ? k_hv_up<RR, T, IDX32, 512, V> : k_hv_up<RR, T, IDX32, 1024, V>;
     unsigned grid = 0;
     hb_status s = persistent_launch_dims(h, kern, threads, smem, n_items, &grid);
     if (s != HB_OK) return s;
     kern<<<grid, threads, smem, st>>>(a, x, y, u.W, n_groups, n_items);
     PD_CUDA(cudaGetLastError());
     return HB_OK;
+}
+
+template <int RR, typename T, bool IDX32>
+hb_status launch_up(hb_handle h, const HvArgs<T> &a, const T *x, T *y, cudaStream_t st, const UpShape &u) {
+    return up_pairs<T>(a.Dd, x, y) ? launch_up_v<RR, T, IDX32, 2>(h, a, x, y, st, u)
+                                   : launch_up_v<RR, T, IDX32, 1>(h, a, x, y, st, u);
 }
 
 template <typename T, bool DO_A>
@@ -209,7 +222,7 @@ hb_status launch_hv_fx_wb(hb_handle h, const FxArgs &a, const int64_t *x, int64_
     return launch_hv_fx_wb_lb<R, NC, 1024>(h, a, x, y, st, threads);
 }
 
-template <int RR, int NC, bool IDX32, int LB>
+template <int RR, int NC, bool IDX32, int LB, int V>
 __global__ void __launch_bounds__(LB) k_hv_fx_up(const FxArgs a, const int64_t *__restrict__ x,
                                                    int64_t *__restrict__ y, int W, uint64_t n_groups,
                                                    uint64_t n_items) {
@@ -217,7 +230,7 @@ __global__ void __launch_bounds__(LB) k_hv_fx_up(const FxArgs a, const int64_t *
     const int S = blockDim.x / W;
     ItemWalk w(n_groups);
     for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x, w.next())
-        hv_fx_up_item<RR, NC, IDX32>(a, x, y, w.j, w.g, W, S, smem);
+        hv_fx_up_item<RR, NC, IDX32, V>(a, x, y, w.j, w.g, W, S, smem);
 }
 
 template <int R, int NC, bool SMEM, int LB, bool DO_A>
@@ -238,19 +251,26 @@ hb_status launch_hv_fx(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *
     return launch_hv_fx_lb<R, NC, SMEM, 1024, DO_A>(h, a, x, y, st, threads);
 }
 
-template <int RR, int NC, bool IDX32>
-hb_status launch_fx_up(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st,
-                       const UpShape &u) {
+template <int RR, int NC, bool IDX32, int V>
+hb_status launch_fx_up_v(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st,
+                         const UpShape &u) {
     const int RA = u.S * RR, threads = u.W * u.S;
     const size_t smem = hv_fx_up_smem_bytes<IDX32>(RA, a.zmax_up);
-    const uint64_t n_groups = (a.Du + RA - 1) / RA, n_items = (a.Dd + u.W - 1) / u.W * n_groups;
-    auto kern = threads <= 512 ? k_hv_fx_up<RR, NC, IDX32, 512> : k_hv_fx_up<RR, NC, IDX32, 1024>;
+    const uint64_t n_groups = (a.Du + RA - 1) / RA, n_items = (a.Dd + (uint64_t)u.W * V - 1) / ((uint64_t)u.W * V) * n_groups;
+    auto kern = threads <= 512 ? k_hv_fx_up<RR, NC, IDX32, 512, V> : k_hv_fx_up<RR, NC, IDX32, 1024, V>;
     unsigned grid = 0;
     hb_status s = persistent_launch_dims(h, kern, threads, smem, n_items, &grid);
     if (s != HB_OK) return s;
     kern<<<grid, threads, smem, st>>>(a, x, y, u.W, n_groups, n_items);
     PD_CUDA(cudaGetLastError());
     return HB_OK;
+}
+
+template <int RR, int NC, bool IDX32>
+hb_status launch_fx_up(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st,
+                       const UpShape &u) {
+    return up_pairs<int64_t>(a.Dd, x, y) ? launch_fx_up_v<RR, NC, IDX32, 2>(h, a, x, y, st, u)
+                                         : launch_fx_up_v<RR, NC, IDX32, 1>(h, a, x, y, st, u);
 }
 
 template <int NC, bool DO_A>

@@ -355,16 +355,25 @@ __device__ __forceinline__ void load_offsets(const OFF *uo, int k, OFF *o) {
     }
 }
 
-// acc += sum_{i < B} coefficient(k + i) * x[off(k + i) + d] in the order i = 0 .. B-1
-template <typename T, typename OFF, int B>
-__device__ __forceinline__ void up_batch_f(const T *__restrict__ x, const OFF *uo, const T *uv, int k, OFF d, T &acc) {
+// V adjacent elements loaded or stored as one vector (V * sizeof(T) bytes, aligned).
+template <typename T, int V>
+struct alignas(sizeof(T) * V) Pack {
+    T v[V];
+};
+
+// acc[v] += sum_{i < B} coefficient(k + i) * x[off(k + i) + d + v] in the order i = 0 .. B-1
+template <typename T, typename OFF, int B, int V>
+__device__ __forceinline__ void up_batch_f(const T *__restrict__ x, const OFF *uo, const T *uv, int k, OFF d,
+                                           T *acc) {
     OFF o[B];
     load_offsets<OFF, B>(uo, k, o);
-    T xv[B];
+    Pack<T, V> xv[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i) xv[i] = x[o[i] + d];
+    for (int i = 0; i < B; ++i) xv[i] = *reinterpret_cast<const Pack<T, V> *>(x + (o[i] + d));
 #pragma unroll
-    for (int i = 0; i < B; ++i) acc += uv[k + i] * xv[i];
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += uv[k + i] * xv[i].v[v];
 }
 
 // Persistent walk over the items (j, g), column-block-major, without a division per item.
@@ -380,10 +389,14 @@ struct ItemWalk {
     }
 };
 
-template <int RR, typename T, bool IDX32>
+// Thread (c, s) takes columns (j W + c) V .. (j W + c) V + V - 1; with V = 2 the
+// caller guarantees D_dn even and 2-element-aligned vectors, so pairs never
+// straddle a row end.
+template <int RR, typename T, bool IDX32, int V>
 __device__ __forceinline__ void hv_up_item(const HvArgs<T> &a, const T *__restrict__ x, T *__restrict__ y,
                                            uint64_t j, uint64_t g, int W, int S, unsigned char *smem) {
     using OFF = typename std::conditional<IDX32, uint32_t, uint64_t>::type;
+    constexpr int B0 = 8 / V;  // loads in flight per batch
     const uint64_t Dd = a.Dd;
     const int RA = S * RR;
     const int zs = up_row_stride(a.zmax_up, 1), zp = up_pow2(a.zmax_up > 0 ? a.zmax_up : 1), lz = __ffs(zp) - 1;
@@ -405,7 +418,7 @@ __device__ __forceinline__ void hv_up_item(const HvArgs<T> &a, const T *__restri
     for (int r = threadIdx.x; r < RA; r += blockDim.x) s_nup[r] = p0 + r < a.Du ? (int)a.cnt_up[p0 + r] : 0;
     __syncthreads();
     const int c = threadIdx.x % W, sl = threadIdx.x / W;
-    const uint64_t d = j * (uint64_t)W + c;
+    const uint64_t d = (j * (uint64_t)W + c) * V;
     if (d >= Dd || sl >= S) return;
 #pragma unroll 1
     for (int i = 0; i < RR; ++i) {
@@ -415,14 +428,22 @@ __device__ __forceinline__ void hv_up_item(const HvArgs<T> &a, const T *__restri
         const int nu = s_nup[r];
         const OFF *uo = s_uoff + r * zs;
         const T *uv = s_uval + r * zs;
-        T accu = T(0);
+        T accu[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) accu[v] = T(0);
         int k = 0;
-        for (; k + 8 <= nu; k += 8) up_batch_f<T, OFF, 8>(x, uo, uv, k, (OFF)d, accu);
-        if (nu - k >= 4) up_batch_f<T, OFF, 4>(x, uo, uv, k, (OFF)d, accu), k += 4;
-        if (nu - k >= 2) up_batch_f<T, OFF, 2>(x, uo, uv, k, (OFF)d, accu), k += 2;
-        if (nu - k >= 1) up_batch_f<T, OFF, 1>(x, uo, uv, k, (OFF)d, accu);
-        T *yp = y + u * Dd + d;
-        *yp = *yp + accu;
+        for (; k + B0 <= nu; k += B0) up_batch_f<T, OFF, B0, V>(x, uo, uv, k, (OFF)d, accu);
+        if constexpr (B0 >= 8)
+            if (nu - k >= 4) up_batch_f<T, OFF, 4, V>(x, uo, uv, k, (OFF)d, accu), k += 4;
+        if constexpr (B0 >= 4)
+            if (nu - k >= 2) up_batch_f<T, OFF, 2, V>(x, uo, uv, k, (OFF)d, accu), k += 2;
+        if constexpr (B0 >= 2)
+            if (nu - k >= 1) up_batch_f<T, OFF, 1, V>(x, uo, uv, k, (OFF)d, accu);
+        Pack<T, V> *yp = reinterpret_cast<Pack<T, V> *>(y + u * Dd + d);
+        Pack<T, V> yv = *yp;
+#pragma unroll
+        for (int v = 0; v < V; ++v) yv.v[v] = yv.v[v] + accu[v];
+        *yp = yv;
     }
 }
 
@@ -432,19 +453,35 @@ __host__ __device__ inline size_t hv_fx_up_smem_bytes(int RA, int zmax) {
     return (((size_t)RA * 8 + 15) & ~(size_t)15) + (size_t)RA * zr * (IDX32 ? 4 : 8);
 }
 
-// exact integer sum of x[off(k + i) + d], i < B (offsets loaded one by one:
-// segment starts are not aligned in the fixed-point lists)
-template <typename OFF, int B>
+// exact integer sums acc[v] += x[off(k + i) + d + v], i < B (offsets loaded one
+// by one: segment starts are not aligned in the fixed-point lists)
+template <typename OFF, int B, int V>
 __device__ __forceinline__ void up_batch_fx(const int64_t *__restrict__ x, const OFF *uo, int k, OFF d,
-                                            int64_t &acc) {
-    int64_t xv[B];
+                                            int64_t *acc) {
+    Pack<int64_t, V> xv[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i) xv[i] = x[uo[k + i] + d];
+    for (int i = 0; i < B; ++i) xv[i] = *reinterpret_cast<const Pack<int64_t, V> *>(x + (uo[k + i] + d));
 #pragma unroll
-    for (int i = 0; i < B; ++i) acc += xv[i];
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += xv[i].v[v];
 }
 
-template <int RR, int NC, bool IDX32>
+// one segment [k, kend) of a row's list: full batches, then the remainder by halves
+template <typename OFF, int V>
+__device__ __forceinline__ void up_segment_fx(const int64_t *__restrict__ x, const OFF *uo, int &k, int kend, OFF d,
+                                              int64_t *acc) {
+    constexpr int B0 = 8 / V;
+    for (; k + B0 <= kend; k += B0) up_batch_fx<OFF, B0, V>(x, uo, k, d, acc);
+    if constexpr (B0 >= 8)
+        if (kend - k >= 4) up_batch_fx<OFF, 4, V>(x, uo, k, d, acc), k += 4;
+    if constexpr (B0 >= 4)
+        if (kend - k >= 2) up_batch_fx<OFF, 2, V>(x, uo, k, d, acc), k += 2;
+    if constexpr (B0 >= 2)
+        if (kend - k >= 1) up_batch_fx<OFF, 1, V>(x, uo, k, d, acc), k += 1;
+}
+
+template <int RR, int NC, bool IDX32, int V>
 __device__ __forceinline__ void hv_fx_up_item(const FxArgs &a, const int64_t *__restrict__ x,
                                               int64_t *__restrict__ y, uint64_t j, uint64_t g, int W, int S,
                                               unsigned char *smem) {
@@ -464,7 +501,7 @@ __device__ __forceinline__ void hv_fx_up_item(const FxArgs &a, const int64_t *__
     }
     __syncthreads();
     const int c = threadIdx.x % W, sl = threadIdx.x / W;
-    const uint64_t d = j * (uint64_t)W + c;
+    const uint64_t d = (j * (uint64_t)W + c) * V;
     if (d >= Dd || sl >= S) return;
 #pragma unroll 1
     for (int i = 0; i < RR; ++i) {
@@ -474,22 +511,24 @@ __device__ __forceinline__ void hv_fx_up_item(const FxArgs &a, const int64_t *__
         const uint64_t ug = s_useg[r];
         const OFF *uo = s_uoff + r * zr;
         int k = 0;
-        uint64_t add = 0;
+        uint64_t add[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) add[v] = 0;
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) {
-            int64_t sum[2] = {0, 0};  // positive, negative sign
+            int64_t pos[V], neg[V];
 #pragma unroll
-            for (int sg = 0; sg < 2; ++sg) {
-                const int kend = k + (int)((ug >> (8 * (2 * cc + sg))) & 0xFFu);
-                for (; k + 8 <= kend; k += 8) up_batch_fx<OFF, 8>(x, uo, k, (OFF)d, sum[sg]);
-                if (kend - k >= 4) up_batch_fx<OFF, 4>(x, uo, k, (OFF)d, sum[sg]), k += 4;
-                if (kend - k >= 2) up_batch_fx<OFF, 2>(x, uo, k, (OFF)d, sum[sg]), k += 2;
-                if (kend - k >= 1) up_batch_fx<OFF, 1>(x, uo, k, (OFF)d, sum[sg]), k += 1;
-            }
-            add += (uint64_t)fx_mul(sum[0] - sum[1], a.Kc[cc], a.Gc[cc]);
+            for (int v = 0; v < V; ++v) pos[v] = neg[v] = 0;
+            up_segment_fx<OFF, V>(x, uo, k, k + (int)((ug >> (16 * cc)) & 0xFFu), (OFF)d, pos);
+            up_segment_fx<OFF, V>(x, uo, k, k + (int)((ug >> (16 * cc + 8)) & 0xFFu), (OFF)d, neg);
+#pragma unroll
+            for (int v = 0; v < V; ++v) add[v] += (uint64_t)fx_mul(pos[v] - neg[v], a.Kc[cc], a.Gc[cc]);
         }
-        int64_t *yp = y + u * Dd + d;
-        *yp = (int64_t)((uint64_t)*yp + add);
+        Pack<int64_t, V> *yp = reinterpret_cast<Pack<int64_t, V> *>(y + u * Dd + d);
+        Pack<int64_t, V> yv = *yp;
+#pragma unroll
+        for (int v = 0; v < V; ++v) yv.v[v] = (int64_t)((uint64_t)yv.v[v] + add[v]);
+        *yp = yv;
     }
 }
 

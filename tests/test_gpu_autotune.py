@@ -10,12 +10,20 @@ from tests.gpu_util import handle_for, need_gpu
 pytestmark = pytest.mark.gpu
 
 
+CLUSTERS = {
+    "3x3_tp_4_4": (lambda: wl.rect_periodic(3, 3, 1.0, -0.3), 5.0, 4, 4),  # D_dn = 126 (even: column pairs)
+    "ring7_3_3": (lambda: wl.ring(7), 2.0, 3, 3),                           # D_dn = 35 (odd: single columns)
+}
+
+
+@pytest.mark.parametrize("cluster", sorted(CLUSTERS))
 @pytest.mark.parametrize("dtype_name", ["float64", "float32", "int64"])
-def test_all_configs_bit_identical(dtype_name):
+def test_all_configs_bit_identical(dtype_name, cluster):
     torch = need_gpu()
     import paper_1707_03974_gb300 as pd
     dtype = getattr(torch, dtype_name)
-    h = handle_for(wl.rect_periodic(3, 3, 1.0, -0.3), 5.0, 4, 4)
+    make, U, nu, nd = CLUSTERS[cluster]
+    h = handle_for(make(), U, nu, nd)
     x = torch.from_numpy(start_vector(3, h.D)).cuda()
     x = pd.hubbard_convert(h, x / x.abs().max(), torch.int64) if dtype_name == "int64" else x.to(dtype)
     ref = pd.hubbard_apply(h, x).cpu()
@@ -25,8 +33,8 @@ def test_all_configs_bit_identical(dtype_name):
                 pd.hubbard_set_hv_config(h, dtype, rows, threads, order)
                 y = pd.hubbard_apply(h, x).cpu()
                 assert torch.equal(y, ref), (rows, threads, order)
-    # split form: row pass then the column-blocked spin-up pass; D_dn = 126 leaves
-    # ragged column blocks for every block width
+    # split form: row pass then the column-blocked spin-up pass; both row lengths
+    # leave ragged column blocks for every block width
     for rows, threads in ((1, 256), (2, 1024)):
         for ub, ut in ((32, 64), (64, 512), (128, 1024), (256, 256)):
             for rr in (1, 2, 4):
