@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the library's default H·v launch configuration")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--hv-config", default=None,
+                   help="JSON H·v launch configuration (keys of hubbard_set_hv_config) instead of the autotuner")
     return p.parse_args()
 
 
@@ -208,7 +210,11 @@ def run_ours(args, world, rank, local):
     beta = torch.zeros(nsteps + 1, dtype=torch.float64, device=dev)
     scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device=dev)
     pd.hubbard_apply(h, V[0], V[1])  # builds the per-spin tables (setup, untimed)
-    tuned = pd.hubbard_autotune(h, V[0], V[1], reps=2) if args.autotune else pd.hubbard_get_hv_config(h, vdt)
+    if args.hv_config:
+        pd.hubbard_set_hv_config(h, vdt, **json.loads(args.hv_config))
+        tuned = pd.hubbard_get_hv_config(h, vdt)
+    else:
+        tuned = pd.hubbard_autotune(h, V[0], V[1], reps=2) if args.autotune else pd.hubbard_get_hv_config(h, vdt)
     torch.cuda.synchronize()
 
     launches = ctypes.c_uint32(0)
@@ -281,6 +287,8 @@ def run_ours(args, world, rank, local):
         P = [torch.empty(D, dtype=torch.float64, device=dev) for _ in range(3)]
         P[0].uniform_(-1.0, 1.0, generator=g)
         P[0] /= P[0].norm()
+        if args.autotune:  # the float64 comparison gets its own tuned launch configuration
+            pd.hubbard_autotune(h, P[0], P[1], reps=2)
         for j in range(args.warmup):
             pd.lanczos_step(h, P[j % 3], P[(j - 1) % 3] if j else None, P[(j + 1) % 3],
                             beta[j - 1:j] if j else None, alpha[j:j + 1], beta[j:j + 1], scratch)
