@@ -209,14 +209,18 @@ hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *opts, const v
                                double *alphas, double *betas, double *E0, hb_lanczos_info *info,
                                void *stream);
 
-/* Bytes of device scratch (per-block partial sums of the reductions) lanczos_step needs. */
+/* Bytes of device scratch (per-block partial sums of the reductions: three
+ * 16-byte sums per block) lanczos_step needs. */
 hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes);
 
 /*
  * One step of the three-term Lanczos recurrence (the building block of
  * lanczos_ground_state, exposed for drivers that keep their own loop):
  *   w = H v - beta_prev * vprev;  alpha = <w, v>;  w -= alpha * v;  beta = ||w||;  w /= beta,
- * after which w holds the next Lanczos vector.
+ * after which w holds the next Lanczos vector.  HB_FX64 takes two vector passes:
+ * the first forms w with the exact sums <w,v>, <w,w>, <v,v>, from which
+ * beta^2 = <w,w> - 2 alpha <w,v> + alpha^2 <v,v> is evaluated in double-double
+ * arithmetic; the second writes (w - alpha v) / beta.
  * dt            element type of v, vprev, w (device vectors of length D; w must not
  *               overlap v or vprev).
  * vprev, beta_prev  previous vector and device scalar; both NULL on the first step.
@@ -225,7 +229,8 @@ hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes);
  * scratch       caller-owned device buffer of lanczos_step_scratch_bytes bytes.
  * ev_hv_begin, ev_hv_end  optional cudaEvent_t (as void*) recorded on `stream`
  *               just before and just after the H·v kernel (a timing hook; NULL to skip).
- * launches      optional host counter, incremented by the number of kernels enqueued (6).
+ * launches      optional host counter, incremented by the number of kernels enqueued
+ *               (H·v: 1, or 2 in the split form; then 3 for HB_FX64, 5 otherwise).
  * Asynchronous on `stream`.
  */
 hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w, const double *beta_prev,

@@ -104,6 +104,8 @@ struct hb_basis {
 // ---- internal entry points shared between translation units ----
 hb_status pd_build_tables(hb_handle h);
 hb_status pd_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st);
+// kernels one pd_apply launches under the handle's configuration for dt
+int pd_hv_launches(hb_handle h, hb_dtype dt);
 void pd_record_error(hb_handle h, hb_status s);
 
 hb_status pd_fx_coefs(hb_handle h, FxCoef *diag /*[PD_MAXL+1]*/, FxCoef *cls /*[PD_FX_MAXC]*/);

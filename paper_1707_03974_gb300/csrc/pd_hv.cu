@@ -367,6 +367,8 @@ hb_status pd_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_
     return apply_part(h, dt, x, y, st, kAll);
 }
 
+int pd_hv_launches(hb_handle h, hb_dtype dt) { return h->hv_cfg[dt].split ? 2 : 1; }
+
 namespace {
 
 void to_public(const HvConfig &c, float ms, hb_hv_config *out) {

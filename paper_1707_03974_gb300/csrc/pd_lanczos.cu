@@ -266,36 +266,6 @@ __device__ __forceinline__ I128 block_sum128(I128 v) {
     return r;  // valid in thread 0
 }
 
-__global__ void k_fx_axpy_dot(int64_t *__restrict__ w, const int64_t *__restrict__ vprev,
-                              const double *__restrict__ beta_prev, const int64_t *__restrict__ v, uint64_t n,
-                              I128 *__restrict__ partials) {
-    I128 acc;
-    const FxCoef b = beta_prev ? fx_coef_dev(*beta_prev) : FxCoef();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        int64_t wi = w[i];
-        if (beta_prev) {
-            wi -= fx_mul(vprev[i], b.K, b.G);
-            w[i] = wi;
-        }
-        i128_add_prod(acc, wi, v[i]);
-    }
-    const I128 s = block_sum128(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
-__global__ void k_fx_axpy_norm(int64_t *__restrict__ w, const int64_t *__restrict__ v,
-                               const double *__restrict__ alpha, uint64_t n, I128 *__restrict__ partials) {
-    I128 acc;
-    const FxCoef al = fx_coef_dev(*alpha);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const int64_t wi = w[i] - fx_mul(v[i], al.K, al.G);
-        w[i] = wi;
-        i128_add_prod(acc, wi, wi);
-    }
-    const I128 s = block_sum128(acc);
-    if (partials && threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
 __global__ void k_fx_scale(int64_t *__restrict__ v, const double *__restrict__ den, uint64_t n) {
     const double d = *den;
     const FxCoef f = fx_coef_dev(d != 0.0 ? 1.0 / d : 0.0);
@@ -312,6 +282,102 @@ __global__ void k_reduce128(const I128 *__restrict__ partials, int nb, double *_
     if (threadIdx.x == 0) {
         const double v = ldexp((double)s.hi * 18446744073709551616.0 + (double)s.lo, sh - 2 * F);
         out[0] = mode == 1 ? sqrt(v) : v;
+    }
+}
+
+// ---- fused fixed-point step: two passes instead of three ----
+// Pass 1 forms w = H v - beta_prev vprev and the exact sums <w, v>, <w, w>,
+// <v, v>; alpha = <w, v> and beta^2 = ||w - alpha v||^2 = <w,w> - 2 alpha <w,v>
+// + alpha^2 <v,v> follow in double-double arithmetic from the exact 128-bit
+// sums (no cancellation loss); pass 2 writes (w - alpha v) / beta.
+__global__ void k_fx_axpy_dot3(int64_t *__restrict__ w, const int64_t *__restrict__ vprev,
+                               const double *__restrict__ beta_prev, const int64_t *__restrict__ v, uint64_t n,
+                               I128 *__restrict__ partials) {
+    I128 swv, sww, svv;
+    const FxCoef b = beta_prev ? fx_coef_dev(*beta_prev) : FxCoef();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        int64_t wi = w[i];
+        const int64_t vi = v[i];
+        if (beta_prev) {
+            wi -= fx_mul(vprev[i], b.K, b.G);
+            w[i] = wi;
+        }
+        i128_add_prod(swv, wi, vi);
+        i128_add_prod(sww, wi, wi);
+        i128_add_prod(svv, vi, vi);
+    }
+    const I128 a = block_sum128(swv);
+    const I128 c = block_sum128(sww);
+    const I128 d = block_sum128(svv);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = a;
+        partials[gridDim.x + blockIdx.x] = c;
+        partials[2 * gridDim.x + blockIdx.x] = d;
+    }
+}
+
+// double-double helpers (Dekker / Knuth error-free transformations)
+struct DD {
+    double h, l;
+};
+__device__ __forceinline__ DD dd_two_sum(double a, double b) {
+    const double s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DD dd_norm(double s, double e) {
+    const double t = s + e;
+    return {t, e - (t - s)};
+}
+__device__ __forceinline__ DD dd_add(DD x, DD y) {
+    DD s = dd_two_sum(x.h, y.h);
+    return dd_norm(s.h, s.l + x.l + y.l);
+}
+__device__ __forceinline__ DD dd_mul_d(DD x, double y) {
+    const double p = x.h * y;
+    return dd_norm(p, fma(x.h, y, -p) + x.l * y);
+}
+// a 128-bit integer times 2^sh as a double-double: the four 32-bit pieces are exact doubles
+__device__ __forceinline__ DD dd_of_i128(I128 s, int sh) {
+    const double h1 = ldexp((double)(int32_t)(uint32_t)((uint64_t)s.hi >> 32), 96 + sh);
+    const double h0 = ldexp((double)(uint32_t)((uint64_t)s.hi & 0xFFFFFFFFu), 64 + sh);
+    const double l1 = ldexp((double)(uint32_t)(s.lo >> 32), 32 + sh);
+    const double l0 = ldexp((double)(uint32_t)(s.lo & 0xFFFFFFFFu), sh);
+    DD r = {h1, 0.0};
+    r = dd_add(r, {h0, 0.0});
+    r = dd_add(r, {l1, 0.0});
+    return dd_add(r, {l0, 0.0});
+}
+
+// alpha = <w, v>; beta = sqrt(<w,w> - 2 alpha <w,v> + alpha^2 <v,v>) with the
+// alpha that pass 2 applies (the float64 value written to *alpha)
+__global__ void k_fx_alpha_beta(const I128 *__restrict__ partials, int nb, double *__restrict__ alpha,
+                                double *__restrict__ beta, int F) {
+    I128 t[3];
+    for (int k = 0; k < 3; ++k) {
+        I128 s;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) i128_add(s, partials[k * nb + i]);
+        t[k] = block_sum128(s);
+    }
+    if (threadIdx.x == 0) {
+        const DD swv = dd_of_i128(t[0], -2 * F), sww = dd_of_i128(t[1], -2 * F), svv = dd_of_i128(t[2], -2 * F);
+        const double al = swv.h + swv.l;
+        DD b2 = dd_add(sww, dd_mul_d(swv, -2.0 * al));
+        b2 = dd_add(b2, dd_mul_d(dd_mul_d(svv, al), al));
+        const double v = b2.h + b2.l;
+        alpha[0] = al;
+        beta[0] = v > 0.0 ? sqrt(v) : 0.0;
+    }
+}
+
+// w = (w - alpha v) / beta  (without the division when !scale)
+__global__ void k_fx_update(int64_t *__restrict__ w, const int64_t *__restrict__ v, const double *__restrict__ alpha,
+                            const double *__restrict__ beta, int scale, uint64_t n) {
+    const FxCoef al = fx_coef_dev(*alpha);
+    const double b = *beta;
+    const FxCoef f = fx_coef_dev(b != 0.0 ? 1.0 / b : 0.0);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t wi = w[i] - fx_mul(v[i], al.K, al.G);
+        w[i] = scale ? fx_mul(wi, f.K, f.G) : wi;
     }
 }
 
@@ -460,8 +526,9 @@ Layout make_layout(hb_handle h, const hb_lanczos_opts &o) {
     L.maxit = o.maxit;
     const uint64_t D = h->D;
     L.nblk = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)h->sm_count * 4, (D + kRedThreads - 1) / kRedThreads));
-    // 16 bytes per partial: a float64 sum, or a 128-bit integer sum for HB_FX64
-    const uint64_t npart = 2ull * L.nblk * (o.reorth ? (uint64_t)(o.maxit + 1) : 1ull);
+    // partial sums per reduction block: three 128-bit integers (the fixed-point
+    // step), or one float64 per block and stored vector (full reorthogonalisation)
+    const uint64_t npart = std::max<uint64_t>(6ull * L.nblk, o.reorth ? (uint64_t)L.nblk * (o.maxit + 1) : 0ull);
     const uint64_t es = o.vec_dtype == HB_F32 ? 4 : 8;
     L.partials = 0;
     L.scal = align256(npart * 8);
@@ -523,6 +590,8 @@ hb_status three_term_step(Solve &s, hb_dtype dt, const T *v, const T *vp, T *w, 
     return HB_OK;
 }
 
+// The fixed-point step in two passes (see k_fx_axpy_dot3): 4 kernel launches
+// after the H·v.
 hb_status three_term_step_fx(Solve &s, const int64_t *v, const int64_t *vp, int64_t *w, const double *beta_prev,
                              double *alpha, double *beta, bool scale, cudaEvent_t ev0, cudaEvent_t ev1) {
     const int nb = s.nblk;
@@ -532,14 +601,15 @@ hb_status three_term_step_fx(Solve &s, const int64_t *v, const int64_t *vp, int6
     hb_status st = pd_apply(s.h, HB_FX64, v, w, s.st);
     if (st != HB_OK) return st;
     if (ev1) PD_CUDA(cudaEventRecord(ev1, s.st));
-    k_fx_axpy_dot<<<nb, kRedThreads, 0, s.st>>>(w, vp, vp ? beta_prev : nullptr, v, s.D, part);
-    k_reduce128<<<1, kFinalThreads, 0, s.st>>>(part, nb, alpha, 0, F);
-    k_fx_axpy_norm<<<nb, kRedThreads, 0, s.st>>>(w, v, alpha, s.D, part);
-    k_reduce128<<<1, kFinalThreads, 0, s.st>>>(part, nb, beta, 1, F);
-    if (scale) k_fx_scale<<<s.grid_vec, kRedThreads, 0, s.st>>>(w, beta, s.D);
+    k_fx_axpy_dot3<<<nb, kRedThreads, 0, s.st>>>(w, vp, vp ? beta_prev : nullptr, v, s.D, part);
+    k_fx_alpha_beta<<<1, kFinalThreads, 0, s.st>>>(part, nb, alpha, beta, F);
+    k_fx_update<<<s.grid_vec, kRedThreads, 0, s.st>>>(w, v, alpha, beta, scale ? 1 : 0, s.D);
     PD_CUDA(cudaGetLastError());
     return HB_OK;
 }
+
+template <typename T>
+constexpr bool kFxScalesInStep = std::is_same<T, int64_t>::value;
 
 template <typename T>
 hb_status step_any(Solve &s, hb_dtype dt, const T *v, const T *vp, T *w, const double *beta_prev, double *alpha,
@@ -579,8 +649,9 @@ hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, b
         T *w = V + (uint64_t)iw * stride;
         T *vp = ip >= 0 ? V + (uint64_t)ip * stride : nullptr;
         if (!reorth) {
+            // the fixed-point step divides by beta in its last pass; float steps divide below
             hb_status st = step_any<T>(s, dt, v, vp, w, vp ? s.d_beta + (j - 1) : nullptr, s.d_alpha + j,
-                                       s.d_beta + j, false, nullptr, nullptr);
+                                       s.d_beta + j, kFxScalesInStep<T>, nullptr, nullptr);
             if (st != HB_OK) return st;
         } else if constexpr (std::is_same<T, int64_t>::value) {
             return HB_ERR_INVALID_ARG;  // full reorthogonalisation is float only
@@ -626,7 +697,7 @@ hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, b
                 return HB_OK;
             }
         }
-        scale_any<T>(s, w, s.d_beta + j);
+        if (reorth || !kFxScalesInStep<T>) scale_any<T>(s, w, s.d_beta + j);
         if (reorth) {
             ip = iv;
             iv = j + 1;
@@ -690,8 +761,16 @@ hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes) {
     hb_lanczos_opts o{};
     o.maxit = 1;
     o.vec_dtype = HB_F64;
-    *bytes = (uint64_t)make_layout(h, o).nblk * 16;  // one 16-byte partial per reduction block
+    *bytes = (uint64_t)make_layout(h, o).nblk * 48;  // three 16-byte partials per reduction block
     return HB_OK;
+}
+
+// reduction blocks of one step (the partial sums above are per block)
+int step_blocks(hb_handle h) {
+    hb_lanczos_opts o{};
+    o.maxit = 1;
+    o.vec_dtype = HB_F64;
+    return make_layout(h, o).nblk;
 }
 
 hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w, const double *beta_prev,
@@ -717,7 +796,7 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
     s.h = h;
     s.st = reinterpret_cast<cudaStream_t>(stream);
     s.D = h->D;
-    s.nblk = (int)(need / 16);
+    s.nblk = step_blocks(h);
     s.partials = static_cast<double *>(scratch);
     s.grid_vec = h->sm_count * 8;
     cudaEvent_t e0 = reinterpret_cast<cudaEvent_t>(ev_hv_begin), e1 = reinterpret_cast<cudaEvent_t>(ev_hv_end);
@@ -730,7 +809,7 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
     else
         st = three_term_step<float>(s, dt, static_cast<const float *>(v), static_cast<const float *>(vprev),
                                     static_cast<float *>(w), beta_prev, alpha, beta, true, e0, e1);
-    if (st == HB_OK && launches) *launches += 6;
+    if (st == HB_OK && launches) *launches += (uint32_t)(pd_hv_launches(h, dt) + (dt == HB_FX64 ? 3 : 5));
     return st;
 }
 
@@ -943,9 +1022,7 @@ extern "C" hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *
     int dev = -1;
     PD_CUDA(cudaGetDevice(&dev));
     if (dev != h->device || dev < 0 || dev >= PD_NOALLOC_MAX_DEVICES) return HB_ERR_INVALID_ARG;
-    uint64_t need = 0;
-    lanczos_step_scratch_bytes(h, &need);
-    const uint64_t nblk = need / 16;  // one float64 partial per block is used here
+    const uint64_t nblk = (uint64_t)step_blocks(h);  // one float64 partial per block is used here
     if (nblk > PD_NOALLOC_PARTIALS) return HB_ERR_NO_MEMORY;  // device wider than the fixed scratch
     double *partials = nullptr;
     {
@@ -972,6 +1049,6 @@ extern "C" hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *
     else
         st = three_term_step<float>(s, dt, static_cast<const float *>(v), static_cast<const float *>(vprev),
                                     static_cast<float *>(w), beta_prev, alpha, beta, true, e0, e1);
-    if (st == HB_OK && launches) *launches += 6;
+    if (st == HB_OK && launches) *launches += (uint32_t)(pd_hv_launches(h, dt) + 5);
     return st;
 }

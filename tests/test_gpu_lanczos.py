@@ -189,6 +189,37 @@ def test_fx64_step_tracks_f64_step(env):
     h.close()
 
 
+@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("dtype_name", ["float64", "int64"])
+def test_step_launch_count_and_unit_norm(env, dtype_name, split):
+    """The launch counter matches the kernels enqueued (H·v 1 or 2, then 3 fixed-point or 5
+    float passes), and the fixed-point step, whose beta comes from the exact sums
+    <w,w> - 2 alpha <w,v> + alpha^2 <v,v>, leaves a vector of unit norm."""
+    import ctypes
+    torch, pd = env
+    dtype = getattr(torch, dtype_name)
+    h = handle_for(wl.rect_periodic(4, 3), 4.0, 4, 4)
+    pd.hubbard_set_hv_config(h, dtype, 0, 0, 1, split=split)
+    x = torch.from_numpy(start_vector(7, h.D)).cuda()
+    x /= x.norm()
+    v = pd.hubbard_convert(h, x, torch.int64) if dtype_name == "int64" else x
+    dev = torch.device("cuda")
+    scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device=dev)
+    a = torch.zeros(2, dtype=torch.float64, device=dev)
+    b = torch.zeros(2, dtype=torch.float64, device=dev)
+    w, w2 = torch.empty_like(v), torch.empty_like(v)
+    n = ctypes.c_uint32(0)
+    pd.lanczos_step(h, v, None, w, None, a[0:1], b[0:1], scratch, launches=n)
+    pd.lanczos_step(h, w, v, w2, b[0:1], a[1:2], b[1:2], scratch, launches=n)
+    torch.cuda.synchronize()
+    per_step = (1 + split) + (3 if dtype_name == "int64" else 5)
+    assert n.value == 2 * per_step
+    for vec in (w, w2):
+        f = pd.hubbard_convert(h, vec, torch.float64) if dtype_name == "int64" else vec
+        assert abs(float(f.norm()) - 1.0) < 1e-14
+    h.close()
+
+
 def test_batch_instances_fx64_sample(env):
     torch, pd = env
     recs = golden("batch64")
