@@ -53,7 +53,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="hubbard4x4_half", choices=sorted(WORKLOADS) + ["batch64", "learned4x4"])
+    p.add_argument("--workload", default="hubbard4x4_half",
+                   choices=sorted(WORKLOADS) + ["batch64", "learned4x4", "start4x4"])
     p.add_argument("--dtype", default="fx64", choices=["f64", "fx64", "f32"],
                    help="Krylov vector type: fixed-point int64 (default, float64-grade accuracy without the "
                         "float64 pipe), float64 (float64 FMAs), float32")
@@ -61,6 +62,8 @@ def parse():
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the library's default H·v launch configuration")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--basis", default="hubbard4x4_half", choices=sorted(WORKLOADS),
+                   help="basis of the start4x4 workload (the start vector is built over all of it)")
     p.add_argument("--hv-config", default=None,
                    help="JSON H·v launch configuration (keys of hubbard_set_hv_config) instead of the autotuner")
     return p.parse_args()
@@ -565,12 +568,69 @@ def run_learned(args, world, rank, local):
     m.close()
 
 
+MLP_FLOPS_PER_STATE = 2 * 128 * (32 + 128)  # the two tensor-core layers of the start-vector network
+
+
+def run_start(args, world, rank, local):
+    """Fused tensor-core inference of the start-vector network over the whole 4x4 half-filled
+    basis (random-init weights of the same architecture): every basis index is unranked on
+    the fly, both layers run on tcgen05, only the start vector is written."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1707_03974_gb300.build import build
+    build()
+    import paper_1707_03974_gb300 as pd
+    import workloads as wl
+    cfg = WORKLOADS[args.basis]
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    h = pd.Handle(cl.L, cl.bonds, cl.t, cfg["U"], cfg["N_up"], cfg["N_dn"])
+    D = h.D
+    m = pd.Mlp(2 * cl.L, seed=1)
+    stream = torch.cuda.current_stream()
+    v = torch.empty(D, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        pd.mlp_start_vector(m, h, torch.float64)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.4)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        v = pd.mlp_start_vector(m, h, torch.float64)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    assert pd.mlp_last_error(m) == "HB_OK" and bool(torch.isfinite(v).all())
+    peaks = measured_peaks() or {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    tflops = MLP_FLOPS_PER_STATE * D / (ms * 1e-3) / 1e12
+    out = {"metric": "start-vector inference Gstates/s (fused tcgen05 MLP over the whole basis)",
+           "value": round(D / (ms * 1e-3) / 1e9, 4), "unit": "Gstates/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16 operands, f32 accumulate, f64 output",
+           "data": "synthetic (random-init weights)", "config": {**cfg, "workload": "start_vector_" + cfg["workload"]},
+           "roofline": {"bound": "tensor", "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s",
+                        "frac": round(tflops / peak, 4), "traffic": None, "kernel": "k_mlp_start<double>",
+                        "flops_per_state": MLP_FLOPS_PER_STATE,
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)" if peaks else "fallback 1900 TFLOP/s"},
+           "gpu_launches": args.steps, "clocks": clk}
+    print(json.dumps(out))
+    m.close()
+    h.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.workload == "learned4x4" and args.impl == "ours":
         if rank == 0:
             run_learned(args, world, rank, local)
+        return
+    if args.workload == "start4x4" and args.impl == "ours":
+        if rank == 0:
+            run_start(args, world, rank, local)
         return
     if args.workload == "batch64" and args.impl == "ours":
         if rank == 0:

@@ -293,18 +293,179 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 }
 
 // start vector entries: v = sign * exp(min(out0, 10) - 10)
+
+// start value of one state: sign(out1) exp(min(out0, 10) - 10), in T (fixed
+// point: scaled by 2^(F-1))
 template <typename T>
-__global__ void k_start_values(const float *__restrict__ out, uint64_t n, T *__restrict__ v, int F) {
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
-        const float a = __expf(fminf(out[2 * r], 10.f) - 10.f);
-        const float s = out[2 * r + 1] >= 0.f ? a : -a;
-        if constexpr (sizeof(T) == 8 && !std::is_floating_point<T>::value)
-            v[r] = (T)__double2ll_rn(ldexp((double)s, F - 1));
-        else
-            v[r] = (T)s;
-    }
+__device__ __forceinline__ T start_value(float out0, float out1, int F) {
+    const float a = __expf(fminf(out0, 10.f) - 10.f);
+    const float s = out1 >= 0.f ? a : -a;
+    if constexpr (sizeof(T) == 8 && !std::is_floating_point<T>::value)
+        return (T)__double2ll_rn(ldexp((double)s, F - 1));
+    else
+        return (T)s;
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference for the start vector: one persistent CTA of 128 threads per
+// 128-state tile.  Thread t builds row t of the occupation-bit tile X (from the
+// per-spin strings of basis index I, i.e. the backward map's tables), thread 0
+// issues Z1 = X W1^T (K = 32) into tensor-memory columns 0..127; each thread
+// reads its row back, applies bias + GELU, rounds to bf16 and writes it as row
+// t of the A operand of Z2 = A1 W2^T (K = 128, columns 128..255); the second
+// epilogue applies bias + GELU, the 2 x 128 output layer and the start-value
+// map and stores only v[I].  The weights stay in shared memory for the CTA's
+// lifetime; nothing of size D but v touches HBM.  Per element the arithmetic
+// is that of mlp_forward followed by the start-value map.
+struct InferSmem {
+    uint8_t W1[kH * kIn * 2];  // B operand of layer 1, core-matrix layout (K = 32)
+    uint8_t W2[kH * kH * 2];   // B operand of layer 2 (K = 128)
+    uint8_t X[kBM * kIn * 2];  // A operand of layer 1
+    uint8_t A1[kBM * kH * 2];  // A operand of layer 2
+    float b1[kH], b2[kH], w3[2 * kH], b3[2];
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_mlp_start(const __nv_bfloat16 *__restrict__ W1b,
+                                                   const __nv_bfloat16 *__restrict__ W2b,
+                                                   const float *__restrict__ params, uint64_t ob1, uint64_t ob2,
+                                                   uint64_t oW3, uint64_t ob3, const uint32_t *__restrict__ str_up,
+                                                   const uint32_t *__restrict__ str_dn, uint64_t D_dn, uint64_t D,
+                                                   int L, int n_bits, T *__restrict__ v, int F, unsigned *err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    constexpr uint32_t kSBO1 = (kIn / 8) * 128, kSBO2 = (kH / 8) * 128;
+    // weights and biases, once per CTA
+    for (int c = tid; c < kH * (kIn / 8); c += 128) {
+        const int r = c / (kIn / 8), kc = c % (kIn / 8);
+        *reinterpret_cast<uint4 *>(S.W1 + tc::core_off(r, kc * 8, kSBO1)) =
+            *reinterpret_cast<const uint4 *>(W1b + (size_t)r * kIn + kc * 8);
+    }
+    for (int c = tid; c < kH * (kH / 8); c += 128) {
+        const int r = c / (kH / 8), kc = c % (kH / 8);
+        *reinterpret_cast<uint4 *>(S.W2 + tc::core_off(r, kc * 8, kSBO2)) =
+            *reinterpret_cast<const uint4 *>(W2b + (size_t)r * kH + kc * 8);
+    }
+    for (int i = tid; i < kH; i += 128) {
+        S.b1[i] = params[ob1 + i];
+        S.b2[i] = params[ob2 + i];
+        S.w3[i] = __bfloat162float(__float2bfloat16_rn(params[oW3 + i]));
+        S.w3[kH + i] = __bfloat162float(__float2bfloat16_rn(params[oW3 + kH + i]));
+    }
+    if (tid < 2) S.b3[tid] = params[ob3 + tid];
+    if (warp == 0) tc::tmem_alloc(&S.tmem, 256);
+    if (tid == 0) tc::mbar_init(&S.bar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint32_t phase = 0;
+    bool ok = true;
+    const uint64_t ntiles = (D + kBM - 1) / kBM;
+    for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int t = tid;
+        const uint64_t I = tile * kBM + t;
+        // row t of X: the occupation bits of basis state I (zero rows past the end)
+        uint64_t state = 0;
+        if (I < D) {
+            const uint64_t u = I / D_dn, d = I - u * D_dn;
+            state = ((uint64_t)str_up[u] << L) | (uint64_t)str_dn[d];
+        }
+#pragma unroll
+        for (int q = 0; q < kIn / 8; ++q) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int p2 = 0; p2 < 4; ++p2) {
+                const int i0 = q * 8 + 2 * p2;
+                const uint32_t lo = (i0 < n_bits && ((state >> i0) & 1ull)) ? 0x3F80u : 0u;  // bf16 1.0
+                const uint32_t hi = (i0 + 1 < n_bits && ((state >> (i0 + 1)) & 1ull)) ? 0x3F80u : 0u;
+                w4[p2] = lo | (hi << 16);
+            }
+            *reinterpret_cast<uint4 *>(S.X + tc::core_off(t, q * 8, kSBO1)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            constexpr uint32_t idesc = tc::make_idesc_bf16(kBM, kH);
+            const uint32_t x0 = tc::smem_u32(S.X), w0 = tc::smem_u32(S.W1);
+#pragma unroll
+            for (int ks = 0; ks < kIn / 16; ++ks)
+                tc::mma_bf16(tmem, tc::make_desc(x0 + ks * 256, 128, kSBO1), tc::make_desc(w0 + ks * 256, 128, kSBO1),
+                             idesc, ks > 0 ? 1u : 0u);
+            tc::commit(&S.bar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&S.bar, phase, kWaitTries) ? 1 : 0) != 0;
+        if (!ok) break;
+        phase ^= 1;
+        tc::fence_after_sync();
+        // epilogue 1: A1[t, :] = bf16(gelu(Z1[t, :] + b1))
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float z[32];
+            tc::tmem_ld32(tmem + lane_base + (uint32_t)c0, z);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int p2 = 0; p2 < 4; ++p2) {
+                    const int i = q * 8 + 2 * p2;
+                    const __nv_bfloat16 a = __float2bfloat16_rn(gelu_f(z[i] + S.b1[c0 + i]));
+                    const __nv_bfloat16 b = __float2bfloat16_rn(gelu_f(z[i + 1] + S.b1[c0 + i + 1]));
+                    w4[p2] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+                }
+                *reinterpret_cast<uint4 *>(S.A1 + tc::core_off(t, c0 + q * 8, kSBO2)) =
+                    make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            constexpr uint32_t idesc = tc::make_idesc_bf16(kBM, kH);
+            const uint32_t a0 = tc::smem_u32(S.A1), w0 = tc::smem_u32(S.W2);
+#pragma unroll
+            for (int ks = 0; ks < kH / 16; ++ks)
+                tc::mma_bf16(tmem + kH, tc::make_desc(a0 + ks * 256, 128, kSBO2),
+                             tc::make_desc(w0 + ks * 256, 128, kSBO2), idesc, ks > 0 ? 1u : 0u);
+            tc::commit(&S.bar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&S.bar, phase, kWaitTries) ? 1 : 0) != 0;
+        if (!ok) break;
+        phase ^= 1;
+        tc::fence_after_sync();
+        // epilogue 2: output layer (W3 at bf16 precision, as mlp_forward) and the start value
+        float o0 = S.b3[0], o1 = S.b3[1];
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float z[32];
+            tc::tmem_ld32(tmem + lane_base + (uint32_t)(kH + c0), z);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float a = gelu_f(z[i] + S.b2[c0 + i]);
+                o0 = fmaf(S.w3[c0 + i], a, o0);
+                o1 = fmaf(S.w3[kH + c0 + i], a, o1);
+            }
+        }
+        tc::fence_before_sync();  // this tile's tensor-memory reads precede the next tile's MMAs
+        if (I < D) v[I] = start_value<T>(o0, o1, F);
+    }
+    if (!ok) {
+        // gave up waiting: record it, then drain (bounded) so no MMA still writes the
+        // tensor memory released below
+        if (tid == 0) atomicOr(err, PD_ERRBIT(HB_ERR_TIMEOUT));
+        tc::mbar_wait(&S.bar, phase, kWaitTries);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
 int grid_of(uint64_t n, int sms) { return (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8)); }
 
 }  // namespace
@@ -536,22 +697,25 @@ hb_status mlp_start_vector(hb_mlp_handle m, hb_handle h, hb_dtype dt, void *v, v
     hb_status s = pd_build_tables(h);
     if (s != HB_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const uint64_t chunk = 1ull << 20;
-    if ((s = ensure_ws(m, chunk)) != HB_OK) return s;
-    for (uint64_t i0 = 0; i0 < h->D; i0 += chunk) {
-        const uint64_t n = std::min(chunk, h->D - i0);
-        const uint64_t n_pad = (n + kBM - 1) / kBM * kBM;
-        k_states_of_range<<<grid_of(n, m->sm_count), 256, 0, st>>>(h->up.str, h->dn.str, h->D_dn, h->L, i0, n,
-                                                                   m->states);
-        k_bits<<<grid_of(n_pad * kIn, m->sm_count), 256, 0, st>>>(m->states, n, n_pad, m->n_in, m->X);
-        if ((s = forward_rows(m, n, n_pad, st)) != HB_OK) return s;
-        if (dt == HB_F32)
-            k_start_values<float><<<grid_of(n, m->sm_count), 256, 0, st>>>(m->out, n, static_cast<float *>(v) + i0, 0);
-        else if (dt == HB_F64)
-            k_start_values<double><<<grid_of(n, m->sm_count), 256, 0, st>>>(m->out, n, static_cast<double *>(v) + i0, 0);
-        else
-            k_start_values<int64_t><<<grid_of(n, m->sm_count), 256, 0, st>>>(m->out, n,
-                                                                             static_cast<int64_t *>(v) + i0, h->fx_frac);
+    const size_t smem = sizeof(InferSmem);
+    const uint64_t ntiles = (h->D + kBM - 1) / kBM;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, 2ull * m->sm_count));
+    const int F = h->fx_frac;
+    if (dt == HB_F32) {
+        PD_CUDA(cudaFuncSetAttribute(k_mlp_start<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mlp_start<float><<<grid, 128, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3, h->up.str,
+                                                   h->dn.str, h->D_dn, h->D, h->L, m->n_in,
+                                                   static_cast<float *>(v), F, m->d_err);
+    } else if (dt == HB_F64) {
+        PD_CUDA(cudaFuncSetAttribute(k_mlp_start<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mlp_start<double><<<grid, 128, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3,
+                                                    h->up.str, h->dn.str, h->D_dn, h->D, h->L, m->n_in,
+                                                    static_cast<double *>(v), F, m->d_err);
+    } else {
+        PD_CUDA(cudaFuncSetAttribute(k_mlp_start<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mlp_start<int64_t><<<grid, 128, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3,
+                                                     h->up.str, h->dn.str, h->D_dn, h->D, h->L, m->n_in,
+                                                     static_cast<int64_t *>(v), F, m->d_err);
     }
     PD_CUDA(cudaGetLastError());
     return HB_OK;

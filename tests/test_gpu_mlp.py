@@ -85,3 +85,57 @@ def test_training_reduces_loss(env):
         pd.mlp_adam_step(m, 3e-3)
     assert losses[-1] < 0.2 * losses[0]
     m.close()
+
+
+def _expected_start(out):
+    """sign(out1) exp(min(out0, 10) - 10), the start-value map, in float64."""
+    return np.where(out[:, 1] >= 0, 1.0, -1.0) * np.exp(np.minimum(out[:, 0].astype(np.float64), 10.0) - 10.0)
+
+
+@pytest.mark.parametrize("dtype_name", ["float32", "float64", "int64"])
+def test_fused_start_vector_matches_forward(env, dtype_name):
+    """The fused tensor-core inference kernel (unranking on the fly) against mlp_forward on
+    every basis state of a small sector (D = 3920: 30 full tiles and a ragged one) and
+    against the float64 oracle of the network."""
+    torch, pd = env
+    from tests.gpu_util import handle_for
+    L = 8
+    h = handle_for(wl.ring(L), 2.0, 4, 3)
+    m = pd.Mlp(2 * L, seed=11)
+    b = Basis(L, 4, 3)
+    assert len(b.combined) == h.D == 3920
+    out = pd.mlp_forward(m, to_dev_u64(b.combined)).cpu().numpy()
+    want = _expected_start(out)
+    v = pd.mlp_start_vector(m, h, getattr(torch, dtype_name))
+    if dtype_name == "int64":
+        got = pd.hubbard_convert(h, v, torch.float64).cpu().numpy() * 2.0  # stored as s / 2
+    else:
+        got = v.double().cpu().numpy()
+    assert np.all(np.sign(got) == np.sign(want))
+    assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-5
+    theta = m.get_params().astype(np.float64)
+    ref, _ = forward(theta, bits_of(b.combined, L), 2 * L, 128, emulate_bf16=True)
+    assert np.max(np.abs(np.log(np.abs(got)) - np.log(np.abs(_expected_start(ref))))) <= 2e-3 * max(
+        1.0, np.max(np.abs(ref)))
+    assert pd.mlp_last_error(m) == "HB_OK"
+    m.close()
+    h.close()
+
+
+def test_fused_start_vector_sampled_at_853776(env):
+    """3x4 cluster, N_up = N_dn = 6 (D = 853,776): 4096 sampled entries against mlp_forward
+    on the unranked states."""
+    torch, pd = env
+    from tests.gpu_util import handle_for
+    h = handle_for(wl.rect_periodic(4, 3), 5.0, 6, 6)
+    m = pd.Mlp(24, seed=5)
+    v = pd.mlp_start_vector(m, h, torch.float32)
+    g = torch.Generator().manual_seed(9)
+    idx = torch.randint(0, h.D, (4096,), generator=g)
+    idx[:2] = torch.tensor([0, h.D - 1])
+    states = pd.paradeisos_unrank(h, idx.cuda())
+    want = _expected_start(pd.mlp_forward(m, states).cpu().numpy())
+    got = v[idx.cuda()].double().cpu().numpy()
+    assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-5
+    m.close()
+    h.close()
