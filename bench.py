@@ -38,6 +38,10 @@ WORKLOADS = {
     # smaller sector of the same cluster, for profiler captures (0.5 GB per vector, still > L2)
     "hubbard4x4_n6": {"workload": "hubbard_4x4_tp-0.3_U8_6up_6dn", "L": 16,
                       "lattice": "4x4 periodic, t=1, t'=-0.3", "U": 8.0, "N_up": 6, "N_dn": 6, "D": 64128064},
+    # the precision workload: 18-site tilted cluster, run with --dtype f32 (float32 vectors)
+    "tilted18_half": {"workload": "hubbard_18site_tilted_U6_half_filling", "L": 18,
+                      "lattice": "18-site tilted square, lattice vectors (3,3), (3,-3), t=1", "U": 6.0,
+                      "N_up": 9, "N_dn": 9, "D": 2363904400},
 }
 COMMON = {"vector_dtype": "f64",
           "step": "one three-term Lanczos iteration (H·v + alpha/beta reductions + vector updates)",
@@ -192,8 +196,8 @@ def run_ours(args, world, rank, local):
     import workloads as wl
 
     dev = torch.device("cuda", local)
-    cl = wl.square_periodic(4, 1.0, -0.3)
     wk = WORKLOADS[args.workload]
+    cl = wl.tilted_18() if wk["L"] == 18 else wl.square_periodic(4, 1.0, -0.3)
     h = pd.Handle(cl.L, cl.bonds, cl.t, wk["U"], wk["N_up"], wk["N_dn"])
     D = h.D
     stream = torch.cuda.current_stream()
@@ -562,6 +566,9 @@ def run_learned(args, world, rank, local):
            "dtype": "bf16 network (tcgen05), f64/int64 Lanczos", "data": "synthetic (method's own ground states)",
            "config": {"workload": "learned start vector", "train_U": [2, 4, 6, 10], "train_samples_per_U": 500000,
                       "hidden": 128, "steps": len(rep.losses) and max(200, args.steps * 50), "batch": 32768},
+           "time_to_E0_speedup_learned_fx64_vs_random_f64": {
+               k: round(sum(r["seconds"] for r in c["random_f64"]) / len(c["random_f64"]) / c["learned_fx64"]["seconds"], 3)
+               for k, c in cases.items()},
            "train_loss_first_last": [rep.losses[0], rep.losses[-1]], "train_seconds": round(rep.seconds, 3),
            "data_seconds": round(t_data, 3), "cases": cases}
     print(json.dumps(out))

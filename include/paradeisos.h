@@ -217,10 +217,12 @@ hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes);
  * One step of the three-term Lanczos recurrence (the building block of
  * lanczos_ground_state, exposed for drivers that keep their own loop):
  *   w = H v - beta_prev * vprev;  alpha = <w, v>;  w -= alpha * v;  beta = ||w||;  w /= beta,
- * after which w holds the next Lanczos vector.  HB_FX64 takes two vector passes:
- * the first forms w with the exact sums <w,v>, <w,w>, <v,v>, from which
- * beta^2 = <w,w> - 2 alpha <w,v> + alpha^2 <v,v> is evaluated in double-double
- * arithmetic; the second writes (w - alpha v) / beta.
+ * after which w holds the next Lanczos vector.  HB_FX64 and HB_F32 take two
+ * vector passes: the first forms w with the sums <w,v>, <w,w>, <v,v> (exact
+ * 128-bit integers, or float32 pairs with exact products), from which
+ * beta^2 = <w,w> - 2 alpha <w,v> + alpha^2 <v,v> is evaluated (double-double /
+ * float64 arithmetic); the second writes (w - alpha v) / beta.  HB_F64 keeps the
+ * textbook three passes.
  * dt            element type of v, vprev, w (device vectors of length D; w must not
  *               overlap v or vprev).
  * vprev, beta_prev  previous vector and device scalar; both NULL on the first step.
@@ -230,7 +232,7 @@ hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes);
  * ev_hv_begin, ev_hv_end  optional cudaEvent_t (as void*) recorded on `stream`
  *               just before and just after the H·v kernel (a timing hook; NULL to skip).
  * launches      optional host counter, incremented by the number of kernels enqueued
- *               (H·v: 1, or 2 in the split form; then 3 for HB_FX64, 5 otherwise).
+ *               (H·v: 1, or 2 in the split form; then 3, or 5 for HB_F64).
  * Asynchronous on `stream`.
  */
 hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w, const double *beta_prev,
@@ -257,8 +259,9 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) and caches it; make that first call before any
  *     stream capture begins.
- *   - A device whose reductions need more than 2048 partial sums (more than
- *     512 SMs) is rejected with HB_ERR_NO_MEMORY.
+ *   - A device whose reductions need more than 2048 partial sums (three per
+ *     reduction block, four blocks per SM: more than 170 SMs) is rejected
+ *     with HB_ERR_NO_MEMORY.
  *   - All calls on a device share the array, which keeps the last call's
  *     contents (nothing in it needs to start at zero: every slot is written
  *     before it is read).  Calls whose kernels overlap on the GPU race on it:

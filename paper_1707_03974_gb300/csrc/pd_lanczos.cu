@@ -76,6 +76,18 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;  // valid in thread 0
 }
 
+// Grid-stride loop over [0, n) that hands f four independent indices at a
+// time (i, i + stride, i + 2 stride, i + 3 stride), so each thread keeps
+// several loads in flight; the remainder one by one.  f(i) must not depend on
+// another index's result.
+template <typename Fn>
+__device__ __forceinline__ void for_each_x4(uint64_t n, Fn f) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) f(i, i + stride, i + 2 * stride, i + 3 * stride);
+    for (; i < n; i += stride) f(i);
+}
+
 // ---------------- vector kernels ----------------
 template <typename T>
 __global__ void k_fill_random(T *__restrict__ v, uint64_t n, uint64_t seed) {
@@ -139,6 +151,84 @@ __global__ void k_scale(T *__restrict__ v, const double *__restrict__ den, uint6
     const T f = d != 0.0 ? (T)(1.0 / d) : T(0);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
         v[i] = v[i] * f;
+}
+
+// ---- float32 step in two passes (as the fixed-point one): pass 1 forms
+// w = H v - beta_prev vprev and the sums <w,v>, <w,w>, <v,v> (float32 pairs,
+// exact products); beta^2 = <w,w> - 2 alpha <w,v> + alpha^2 <v,v> in float64;
+// pass 2 writes (w - alpha v) * (1 / beta), the same float32 operations the
+// recurrence replay (k_regen_f32) performs.
+__global__ void k_axpy_dot3_f32(float *__restrict__ w, const float *__restrict__ vprev,
+                                const double *__restrict__ beta_prev, const float *__restrict__ v, uint64_t n,
+                                double *__restrict__ partials) {
+    AccF32x2 swv, sww, svv;
+    const float b = beta_prev ? (float)(*beta_prev) : 0.f;
+    auto one = [&](uint64_t i, float wi, float vi) {
+        swv.add_prod(wi, vi);
+        sww.add_prod(wi, wi);
+        svv.add_prod(vi, vi);
+    };
+    for_each_x4(n, [&](uint64_t i0, auto... rest) {
+        constexpr int U = 1 + sizeof...(rest);
+        const uint64_t idx[U] = {i0, rest...};
+        float wv[U], vv[U], pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            wv[u] = w[idx[u]];
+            vv[u] = v[idx[u]];
+            pv[u] = beta_prev ? vprev[idx[u]] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (beta_prev) {
+                wv[u] = wv[u] - b * pv[u];
+                w[idx[u]] = wv[u];
+            }
+            one(idx[u], wv[u], vv[u]);
+        }
+    });
+    const double a = block_sum(swv.value());
+    const double c = block_sum(sww.value());
+    const double d = block_sum(svv.value());
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = a;
+        partials[gridDim.x + blockIdx.x] = c;
+        partials[2 * gridDim.x + blockIdx.x] = d;
+    }
+}
+
+__global__ void k_alpha_beta_f32(const double *__restrict__ partials, int nb, double *__restrict__ alpha,
+                                 double *__restrict__ beta) {
+    double t[3];
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partials[k * nb + i];
+        t[k] = block_sum(s);
+    }
+    if (threadIdx.x == 0) {
+        const double al = t[0];
+        // the float32 value of alpha is what pass 2 applies
+        const double af = (double)(float)al;
+        const double b2 = t[1] - 2.0 * af * t[0] + af * af * t[2];
+        alpha[0] = al;
+        beta[0] = b2 > 0.0 ? sqrt(b2) : 0.0;
+    }
+}
+
+__global__ void k_update_f32(float *__restrict__ w, const float *__restrict__ v, const double *__restrict__ alpha,
+                             const double *__restrict__ beta, int scale, uint64_t n) {
+    const float al = (float)(*alpha);
+    const double bb = *beta;
+    const float f = scale ? (bb != 0.0 ? (float)(1.0 / bb) : 0.f) : 1.f;
+    for_each_x4(n, [&](uint64_t i0, auto... rest) {
+        constexpr int U = 1 + sizeof...(rest);
+        const uint64_t idx[U] = {i0, rest...};
+        float wv[U], vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) wv[u] = w[idx[u]], vv[u] = v[idx[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[idx[u]] = scale ? (wv[u] - al * vv[u]) * f : wv[u] - al * vv[u];
+    });
 }
 
 // Full reorthogonalisation: partial dots of w with the stored vectors V[0..m),
@@ -295,17 +385,27 @@ __global__ void k_fx_axpy_dot3(int64_t *__restrict__ w, const int64_t *__restric
                                I128 *__restrict__ partials) {
     I128 swv, sww, svv;
     const FxCoef b = beta_prev ? fx_coef_dev(*beta_prev) : FxCoef();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        int64_t wi = w[i];
-        const int64_t vi = v[i];
-        if (beta_prev) {
-            wi -= fx_mul(vprev[i], b.K, b.G);
-            w[i] = wi;
+    for_each_x4(n, [&](uint64_t i0, auto... rest) {
+        constexpr int U = 1 + sizeof...(rest);
+        const uint64_t idx[U] = {i0, rest...};
+        int64_t wv[U], vv[U], pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            wv[u] = w[idx[u]];
+            vv[u] = v[idx[u]];
+            pv[u] = beta_prev ? vprev[idx[u]] : 0;
         }
-        i128_add_prod(swv, wi, vi);
-        i128_add_prod(sww, wi, wi);
-        i128_add_prod(svv, vi, vi);
-    }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (beta_prev) {
+                wv[u] -= fx_mul(pv[u], b.K, b.G);
+                w[idx[u]] = wv[u];
+            }
+            i128_add_prod(swv, wv[u], vv[u]);
+            i128_add_prod(sww, wv[u], wv[u]);
+            i128_add_prod(svv, vv[u], vv[u]);
+        }
+    });
     const I128 a = block_sum128(swv);
     const I128 c = block_sum128(sww);
     const I128 d = block_sum128(svv);
@@ -375,10 +475,18 @@ __global__ void k_fx_update(int64_t *__restrict__ w, const int64_t *__restrict__
     const FxCoef al = fx_coef_dev(*alpha);
     const double b = *beta;
     const FxCoef f = fx_coef_dev(b != 0.0 ? 1.0 / b : 0.0);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const int64_t wi = w[i] - fx_mul(v[i], al.K, al.G);
-        w[i] = scale ? fx_mul(wi, f.K, f.G) : wi;
-    }
+    for_each_x4(n, [&](uint64_t i0, auto... rest) {
+        constexpr int U = 1 + sizeof...(rest);
+        const uint64_t idx[U] = {i0, rest...};
+        int64_t wv[U], vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) wv[u] = w[idx[u]], vv[u] = v[idx[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t wi = wv[u] - fx_mul(vv[u], al.K, al.G);
+            w[idx[u]] = scale ? fx_mul(wi, f.K, f.G) : wi;
+        }
+    });
 }
 
 // Uniform [-1, 1) start vector in fixed point: SplitMix64 output k = z >> 11
@@ -581,11 +689,17 @@ hb_status three_term_step(Solve &s, hb_dtype dt, const T *v, const T *vp, T *w, 
     hb_status st = pd_apply(s.h, dt, v, w, s.st);
     if (st != HB_OK) return st;
     if (ev1) PD_CUDA(cudaEventRecord(ev1, s.st));
-    k_axpy_dot<T><<<s.nblk, kRedThreads, 0, s.st>>>(w, vp, vp ? beta_prev : nullptr, v, s.D, s.partials);
-    k_reduce<<<1, kFinalThreads, 0, s.st>>>(s.partials, s.nblk, alpha, 0);
-    k_axpy_norm<T><<<s.nblk, kRedThreads, 0, s.st>>>(w, v, alpha, s.D, s.partials);
-    k_reduce<<<1, kFinalThreads, 0, s.st>>>(s.partials, s.nblk, beta, 1);
-    if (scale) k_scale<T><<<s.grid_vec, kRedThreads, 0, s.st>>>(w, beta, s.D);
+    if constexpr (std::is_same<T, float>::value) {  // two passes, see k_axpy_dot3_f32
+        k_axpy_dot3_f32<<<s.nblk, kRedThreads, 0, s.st>>>(w, vp, vp ? beta_prev : nullptr, v, s.D, s.partials);
+        k_alpha_beta_f32<<<1, kFinalThreads, 0, s.st>>>(s.partials, s.nblk, alpha, beta);
+        k_update_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(w, v, alpha, beta, scale ? 1 : 0, s.D);
+    } else {  // float64: the textbook three passes (the plain method)
+        k_axpy_dot<T><<<s.nblk, kRedThreads, 0, s.st>>>(w, vp, vp ? beta_prev : nullptr, v, s.D, s.partials);
+        k_reduce<<<1, kFinalThreads, 0, s.st>>>(s.partials, s.nblk, alpha, 0);
+        k_axpy_norm<T><<<s.nblk, kRedThreads, 0, s.st>>>(w, v, alpha, s.D, s.partials);
+        k_reduce<<<1, kFinalThreads, 0, s.st>>>(s.partials, s.nblk, beta, 1);
+        if (scale) k_scale<T><<<s.grid_vec, kRedThreads, 0, s.st>>>(w, beta, s.D);
+    }
     PD_CUDA(cudaGetLastError());
     return HB_OK;
 }
@@ -608,8 +722,9 @@ hb_status three_term_step_fx(Solve &s, const int64_t *v, const int64_t *vp, int6
     return HB_OK;
 }
 
+// the fixed-point and float32 steps divide by beta in their last pass
 template <typename T>
-constexpr bool kFxScalesInStep = std::is_same<T, int64_t>::value;
+constexpr bool kScalesInStep = !std::is_same<T, double>::value;
 
 template <typename T>
 hb_status step_any(Solve &s, hb_dtype dt, const T *v, const T *vp, T *w, const double *beta_prev, double *alpha,
@@ -649,9 +764,9 @@ hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, b
         T *w = V + (uint64_t)iw * stride;
         T *vp = ip >= 0 ? V + (uint64_t)ip * stride : nullptr;
         if (!reorth) {
-            // the fixed-point step divides by beta in its last pass; float steps divide below
+            // the fixed-point and float32 steps divide by beta in their last pass, float64 below
             hb_status st = step_any<T>(s, dt, v, vp, w, vp ? s.d_beta + (j - 1) : nullptr, s.d_alpha + j,
-                                       s.d_beta + j, kFxScalesInStep<T>, nullptr, nullptr);
+                                       s.d_beta + j, kScalesInStep<T>, nullptr, nullptr);
             if (st != HB_OK) return st;
         } else if constexpr (std::is_same<T, int64_t>::value) {
             return HB_ERR_INVALID_ARG;  // full reorthogonalisation is float only
@@ -697,7 +812,7 @@ hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, b
                 return HB_OK;
             }
         }
-        if (reorth || !kFxScalesInStep<T>) scale_any<T>(s, w, s.d_beta + j);
+        if (reorth || !kScalesInStep<T>) scale_any<T>(s, w, s.d_beta + j);
         if (reorth) {
             ip = iv;
             iv = j + 1;
@@ -809,7 +924,7 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
     else
         st = three_term_step<float>(s, dt, static_cast<const float *>(v), static_cast<const float *>(vprev),
                                     static_cast<float *>(w), beta_prev, alpha, beta, true, e0, e1);
-    if (st == HB_OK && launches) *launches += (uint32_t)(pd_hv_launches(h, dt) + (dt == HB_FX64 ? 3 : 5));
+    if (st == HB_OK && launches) *launches += (uint32_t)(pd_hv_launches(h, dt) + (dt == HB_F64 ? 5 : 3));
     return st;
 }
 
@@ -987,7 +1102,7 @@ hb_status lanczos_ritz_vector_f32(hb_handle h, const hb_lanczos_opts *o, const v
 // Allocation-free variant of lanczos_step.
 //
 // The only scratch lanczos_step needs is one float64 partial sum per reduction
-// block.  This variant keeps that scratch in a fixed file-scope device array,
+// block (three for the float32 step's fused sums).  This variant keeps that scratch in a fixed file-scope device array,
 // so neither the library nor the caller allocates anything per call.  In host
 // code `g_noalloc_partials` names a host-side shadow, not device memory: its
 // device address is looked up once per device with cudaGetSymbolAddress and
@@ -1022,8 +1137,8 @@ extern "C" hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *
     int dev = -1;
     PD_CUDA(cudaGetDevice(&dev));
     if (dev != h->device || dev < 0 || dev >= PD_NOALLOC_MAX_DEVICES) return HB_ERR_INVALID_ARG;
-    const uint64_t nblk = (uint64_t)step_blocks(h);  // one float64 partial per block is used here
-    if (nblk > PD_NOALLOC_PARTIALS) return HB_ERR_NO_MEMORY;  // device wider than the fixed scratch
+    const uint64_t nblk = (uint64_t)step_blocks(h);  // up to three float64 partials per block are used here
+    if (3 * nblk > PD_NOALLOC_PARTIALS) return HB_ERR_NO_MEMORY;  // device wider than the fixed scratch
     double *partials = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -1049,6 +1164,6 @@ extern "C" hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *
     else
         st = three_term_step<float>(s, dt, static_cast<const float *>(v), static_cast<const float *>(vprev),
                                     static_cast<float *>(w), beta_prev, alpha, beta, true, e0, e1);
-    if (st == HB_OK && launches) *launches += (uint32_t)(pd_hv_launches(h, dt) + 5);
+    if (st == HB_OK && launches) *launches += (uint32_t)(pd_hv_launches(h, dt) + (dt == HB_F64 ? 5 : 3));
     return st;
 }

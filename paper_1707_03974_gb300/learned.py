@@ -97,33 +97,44 @@ def solve_from(h: B.Handle, dtype, v0=None, seed: int = 0, tol: float = 1e-10, f
             "seconds": time.perf_counter() - t0}
 
 
+def _timed_start(m: B.Mlp, h: B.Handle, dtype):
+    """The network's start vector in `dtype` and the seconds its build took."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    v = B.mlp_start_vector(m, h, dtype)
+    torch.cuda.synchronize()
+    return v, time.perf_counter() - t0
+
+
+def tune(h: B.Handle):
+    """Autotune the H·v launch configuration of every vector type on this handle (setup, not timed)."""
+    import torch
+    for dt in (torch.float64, torch.int64, torch.float32):
+        x = torch.zeros(h.D, dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        B.hubbard_autotune(h, x, y, reps=2)
+        del x, y
+    torch.cuda.empty_cache()
+
+
 def compare(m: B.Mlp, h: B.Handle, psi=None, seeds=(0,)) -> Dict:
     """Iterations and wall time to E0 at 1e-10: learned start vs random starts (float64 and fixed point),
-    plus the mixed float32 + fixed-point solve from the learned start (start-vector build time included)."""
+    plus the mixed float32 + fixed-point solve from the learned start.  A learned run's seconds include
+    building its start vector on the GPU; every run uses the handle's autotuned H·v."""
     import torch
+    tune(h)
     out = {"random_f64": [solve_from(h, torch.float64, seed=s) for s in seeds]}
     out["random_fx64"] = [solve_from(h, torch.int64, seed=s) for s in seeds]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    v64 = B.mlp_start_vector(m, h, torch.float64)
-    torch.cuda.synchronize()
-    t_build = time.perf_counter() - t0
-    r = solve_from(h, torch.float64, v0=v64)
-    r["seconds"] += t_build
-    out["learned_f64"] = r
-    t0 = time.perf_counter()
-    vfx = B.mlp_start_vector(m, h, torch.int64)
-    torch.cuda.synchronize()
-    r = solve_from(h, torch.int64, v0=vfx)
-    r["seconds"] += time.perf_counter() - t0
-    out["learned_fx64"] = r
-    t0 = time.perf_counter()
-    v32 = B.mlp_start_vector(m, h, torch.float32)
-    torch.cuda.synchronize()
-    r = solve_from(h, torch.float32, v0=v32, fp64_finish="fx64")
-    r["seconds"] += time.perf_counter() - t0
-    out["learned_mixed_f32_fx64"] = r
-    out["start_vector_seconds"] = t_build
+    for name, dt, finish in (("learned_f64", torch.float64, False), ("learned_fx64", torch.int64, False),
+                             ("learned_mixed_f32_fx64", torch.float32, "fx64")):
+        v0, t_build = _timed_start(m, h, dt)
+        r = solve_from(h, dt, v0=v0, fp64_finish=finish)
+        r["seconds"] += t_build
+        r["start_vector_seconds"] = t_build
+        out[name] = r
+        del v0
+    out["start_vector_seconds"] = out["learned_f64"]["start_vector_seconds"]
     if psi is not None:
         out["overlap"] = overlap(m, h, psi)
     return out

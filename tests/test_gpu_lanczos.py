@@ -190,11 +190,11 @@ def test_fx64_step_tracks_f64_step(env):
 
 
 @pytest.mark.parametrize("split", [0, 1])
-@pytest.mark.parametrize("dtype_name", ["float64", "int64"])
+@pytest.mark.parametrize("dtype_name", ["float64", "int64", "float32"])
 def test_step_launch_count_and_unit_norm(env, dtype_name, split):
-    """The launch counter matches the kernels enqueued (H·v 1 or 2, then 3 fixed-point or 5
-    float passes), and the fixed-point step, whose beta comes from the exact sums
-    <w,w> - 2 alpha <w,v> + alpha^2 <v,v>, leaves a vector of unit norm."""
+    """The launch counter matches the kernels enqueued (H·v 1 or 2, then 3 for the two-pass
+    fixed-point and float32 steps or 5 for float64), and a step whose beta comes from the sums
+    <w,w> - 2 alpha <w,v> + alpha^2 <v,v> leaves a vector of unit norm."""
     import ctypes
     torch, pd = env
     dtype = getattr(torch, dtype_name)
@@ -202,7 +202,7 @@ def test_step_launch_count_and_unit_norm(env, dtype_name, split):
     pd.hubbard_set_hv_config(h, dtype, 0, 0, 1, split=split)
     x = torch.from_numpy(start_vector(7, h.D)).cuda()
     x /= x.norm()
-    v = pd.hubbard_convert(h, x, torch.int64) if dtype_name == "int64" else x
+    v = pd.hubbard_convert(h, x, torch.int64) if dtype_name == "int64" else x.to(dtype)
     dev = torch.device("cuda")
     scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device=dev)
     a = torch.zeros(2, dtype=torch.float64, device=dev)
@@ -212,11 +212,12 @@ def test_step_launch_count_and_unit_norm(env, dtype_name, split):
     pd.lanczos_step(h, v, None, w, None, a[0:1], b[0:1], scratch, launches=n)
     pd.lanczos_step(h, w, v, w2, b[0:1], a[1:2], b[1:2], scratch, launches=n)
     torch.cuda.synchronize()
-    per_step = (1 + split) + (3 if dtype_name == "int64" else 5)
+    per_step = (1 + split) + (5 if dtype_name == "float64" else 3)
     assert n.value == 2 * per_step
+    tol = 1e-6 if dtype_name == "float32" else 1e-14
     for vec in (w, w2):
-        f = pd.hubbard_convert(h, vec, torch.float64) if dtype_name == "int64" else vec
-        assert abs(float(f.norm()) - 1.0) < 1e-14
+        f = pd.hubbard_convert(h, vec, torch.float64) if dtype_name == "int64" else vec.double()
+        assert abs(float(f.norm()) - 1.0) < tol
     h.close()
 
 
