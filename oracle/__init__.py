@@ -14,7 +14,10 @@ Definitions used (each function cites the passage it follows):
 * the Hamiltonian is Eq. 1 with the fermion sign fixed by the normal ordering of
   Sec. II A (spin-up creators left of spin-down, higher site index to the left);
 * ground energies come from dense ``numpy.linalg.eigh`` on small clusters and a
-  textbook Lanczos iteration (which the paper cites but does not specify).
+  textbook Lanczos iteration (which the paper cites but does not specify);
+* the momentum-space sectors (Sec. IV A, ``momentum.py``) are ascending lists of
+  (up, dn) strings over the single-particle momenta with fixed total momentum,
+  and their Hamiltonian is Eq. 4 term by term.
 
 Parity status: every function here is pinned by tests against values printed in
 the paper or fixed by mathematics (closed forms, invariants, brute force), except
