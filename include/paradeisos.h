@@ -82,6 +82,26 @@ const char *hb_status_string(hb_status s);
  */
 hb_status hubbard_basis_create(int L, int n_bonds, const int32_t *bonds, const double *t, double U,
                                int N_up, int N_dn, hb_handle *out);
+
+/*
+ * Create the Hubbard problem in one momentum sector (Sec. IV A, Eq. 4):
+ *   H = sum_{k sigma} eps_k n_{k sigma} + (U/N) sum_{k,k',q} c+_{k+q up} c+_{k'-q dn} c_{k' dn} c_{k up}
+ * on an Lx x Ly periodic cluster (Ly = 1: a ring of Lx sites), N = Lx Ly, 2 <= N <= 32,
+ * eps_k = -2t (cos kx + cos ky) - 4t' cos kx cos ky (-2t cos k on a ring).
+ * Bit i of a spin string is the occupation of momentum k_i = 2 pi (mx/Lx, my/Ly),
+ * i = mx + Lx my; states passed to paradeisos_rank / paradeisos_unrank are
+ * (up << N) | dn over these bits.  The sector has total momentum
+ * K = 2 pi (Kx/Lx, Ky/Ly), 0 <= Kx < Lx, 0 <= Ky < Ly; its states are indexed by the
+ * spin-full maps of Sec. IV A with the tables C_i^m(k) and C~_i^m(k; N_dn) (Eq. 6),
+ * i.e. in ascending order of (up << N) | dn.  An empty sector is HB_ERR_INVALID_ARG.
+ * The handle works with hubbard_basis_dim (D = sector dimension), paradeisos_rank /
+ * unrank, hubbard_apply (HB_F64, HB_F32, HB_FX64), hubbard_row_entries,
+ * hubbard_set_U, hubbard_autotune (one launch shape: it only times it),
+ * lanczos_step(_noalloc) and lanczos_ground_state; not with the batch or MLP calls.
+ * All tables (moves of every spin string for every q) are built here, synchronously.
+ */
+hb_status hubbard_basis_create_k(int Lx, int Ly, double t, double tp, double U, int N_up, int N_dn, int Kx, int Ky,
+                                 hb_handle *out);
 hb_status hubbard_basis_destroy(hb_handle h);
 /* D, D_up = C(L,N_up), D_dn = C(L,N_dn); any pointer may be NULL. */
 hb_status hubbard_basis_dim(hb_handle h, uint64_t *D, uint64_t *D_up, uint64_t *D_dn);

@@ -13,7 +13,8 @@ from ._binding import (HB_F32, HB_F64, HB_FX64, Batch, Handle, Mlp, mlp_adam_ste
                        hubbard_row_entries, hubbard_set_U, lanczos_ground_state, lanczos_ritz_vector_f32, lanczos_step,
                        lanczos_step_noalloc, lanczos_step_scratch_bytes, load, paradeisos_rank, paradeisos_unrank)
 
-EXPORTED_SYMBOLS = ("hb_status_string", "hubbard_basis_create", "hubbard_basis_destroy", "hubbard_basis_dim",
+EXPORTED_SYMBOLS = ("hb_status_string", "hubbard_basis_create", "hubbard_basis_create_k", "hubbard_basis_destroy",
+                    "hubbard_basis_dim",
                     "hubbard_set_U", "paradeisos_rank", "paradeisos_unrank", "hubbard_apply", "hubbard_row_entries",
                     "hubbard_last_error", "lanczos_workspace_bytes", "lanczos_ground_state", "hb_tridiag_lowest",
                     "lanczos_step_scratch_bytes", "lanczos_step", "lanczos_step_noalloc",

@@ -66,6 +66,7 @@ def load():
     sig = {
         "hb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "hubbard_basis_create": (ctypes.c_int, [I32, I32, P, P, D, I32, I32, ctypes.POINTER(P)]),
+        "hubbard_basis_create_k": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
         "hubbard_basis_destroy": (ctypes.c_int, [P]),
         "hubbard_basis_dim": (ctypes.c_int, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]),
         "hubbard_set_U": (ctypes.c_int, [P, D]),
@@ -152,6 +153,24 @@ class Handle:
         D, Du, Dd = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(lib.hubbard_basis_dim(h, ctypes.byref(D), ctypes.byref(Du), ctypes.byref(Dd)), "hubbard_basis_dim")
         self.D, self.D_up, self.D_dn = D.value, Du.value, Dd.value
+
+    @classmethod
+    def momentum(cls, Lx: int, Ly: int, t: float, tp: float, U: float, N_up: int, N_dn: int, Kx: int, Ky: int):
+        """Handle of one momentum sector (hubbard_basis_create_k): Lx x Ly periodic cluster (Ly = 1: ring),
+        total momentum 2 pi (Kx/Lx, Ky/Ly)."""
+        lib = load()
+        self = cls.__new__(cls)
+        h = ctypes.c_void_p()
+        _check(lib.hubbard_basis_create_k(int(Lx), int(Ly), float(t), float(tp), float(U), int(N_up), int(N_dn),
+                                          int(Kx), int(Ky), ctypes.byref(h)), "hubbard_basis_create_k")
+        self._h = h
+        self.L, self.N_up, self.N_dn, self.U = int(Lx * Ly), int(N_up), int(N_dn), float(U)
+        self.n_bonds = 0
+        self.Lx, self.Ly, self.K = int(Lx), int(Ly), (int(Kx), int(Ky))
+        D, Du, Dd = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib.hubbard_basis_dim(h, ctypes.byref(D), ctypes.byref(Du), ctypes.byref(Dd)), "hubbard_basis_dim")
+        self.D, self.D_up, self.D_dn = D.value, Du.value, Dd.value
+        return self
 
     @property
     def ptr(self):

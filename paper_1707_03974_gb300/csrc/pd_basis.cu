@@ -647,6 +647,7 @@ hb_status hubbard_basis_create(int L, int n_bonds, const int32_t *bonds, const d
 
 hb_status hubbard_basis_destroy(hb_handle h) {
     if (!h) return HB_ERR_INVALID_ARG;
+    pd_k_free(h->ks);
     free_spin(h->up);
     if (!h->same_spin_tables) free_spin(h->dn);
     cudaFree(h->d_binom);
@@ -699,6 +700,7 @@ hb_status hubbard_set_U(hb_handle h, double U) {
 hb_status paradeisos_rank(hb_handle h, const uint64_t *states, uint64_t *idx, uint64_t n, void *stream) {
     if (!h || (n > 0 && (!states || !idx))) return HB_ERR_INVALID_ARG;
     if (n == 0) return HB_OK;
+    if (h->ks) return pd_k_rank(h, states, idx, n, as_stream(stream));
     k_rank<<<grid_for(n, h->sm_count), kThreads, 0, as_stream(stream)>>>(h->d_binom, states, idx, n, h->L, h->N_up,
                                                                          h->N_dn, h->D_dn, h->d_err);
     PD_CUDA(cudaGetLastError());
@@ -708,6 +710,7 @@ hb_status paradeisos_rank(hb_handle h, const uint64_t *states, uint64_t *idx, ui
 hb_status paradeisos_unrank(hb_handle h, const uint64_t *idx, uint64_t *states, uint64_t n, void *stream) {
     if (!h || (n > 0 && (!states || !idx))) return HB_ERR_INVALID_ARG;
     if (n == 0) return HB_OK;
+    if (h->ks) return pd_k_unrank(h, idx, states, n, as_stream(stream));
     k_unrank<<<grid_for(n, h->sm_count), kThreads, 0, as_stream(stream)>>>(h->d_binom, idx, states, n, h->L,
                                                                            h->N_up, h->N_dn, h->D_dn, h->D, h->d_err);
     PD_CUDA(cudaGetLastError());
@@ -719,6 +722,7 @@ hb_status hubbard_row_entries(hb_handle h, uint64_t row0, uint32_t nrows, uint32
     if (!h || (nrows > 0 && (!cols || !vals || !counts)) || max_entries == 0) return HB_ERR_INVALID_ARG;
     if (row0 > h->D || nrows > h->D - row0) return HB_ERR_INVALID_ARG;
     if (nrows == 0) return HB_OK;
+    if (h->ks) return pd_k_row_entries(h, row0, nrows, max_entries, cols, vals, counts, as_stream(stream));
     hb_status s = pd_build_tables(h);
     if (s != HB_OK) return s;
     const int blocks = (int)((nrows + 127) / 128);

@@ -73,6 +73,8 @@ struct HvConfig {
     int up_rows = 0;     // spin-up pass: rows per thread, 1, 2 or 4 (0 = 1)
 };
 
+struct KSpace;  // momentum-sector tables (pd_kspace.cu)
+
 struct hb_basis {
     int L = 0, N_up = 0, N_dn = 0, n_bonds = 0;
     double U = 0.0;
@@ -99,6 +101,9 @@ struct hb_basis {
     int n_classes = 0;
     double class_t[PD_FX_MAXC] = {0, 0, 0, 0};
     int32_t *d_bond_class = nullptr;  // [n_bonds]
+    // momentum-space handle (Sec. IV A): L is the number of momenta, D the
+    // sector dimension; H·v, ranks and rows go through pd_k_* below
+    KSpace *ks = nullptr;
 };
 
 // ---- internal entry points shared between translation units ----
@@ -107,6 +112,13 @@ hb_status pd_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_
 // kernels one pd_apply launches under the handle's configuration for dt
 int pd_hv_launches(hb_handle h, hb_dtype dt);
 void pd_record_error(hb_handle h, hb_status s);
+// momentum-space counterparts (pd_kspace.cu)
+hb_status pd_k_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st);
+hb_status pd_k_rank(hb_handle h, const uint64_t *states, uint64_t *idx, uint64_t n, cudaStream_t st);
+hb_status pd_k_unrank(hb_handle h, const uint64_t *idx, uint64_t *states, uint64_t n, cudaStream_t st);
+hb_status pd_k_row_entries(hb_handle h, uint64_t row0, uint32_t nrows, uint32_t max_entries, uint64_t *cols,
+                           double *vals, uint32_t *counts, cudaStream_t st);
+void pd_k_free(KSpace *ks);
 
 hb_status pd_fx_coefs(hb_handle h, FxCoef *diag /*[PD_MAXL+1]*/, FxCoef *cls /*[PD_FX_MAXC]*/);
 

@@ -364,10 +364,11 @@ hb_status apply_part(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStrea
 }  // namespace
 
 hb_status pd_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st) {
+    if (h->ks) return pd_k_apply(h, dt, x, y, st);
     return apply_part(h, dt, x, y, st, kAll);
 }
 
-int pd_hv_launches(hb_handle h, hb_dtype dt) { return h->hv_cfg[dt].split ? 2 : 1; }
+int pd_hv_launches(hb_handle h, hb_dtype dt) { return !h->ks && h->hv_cfg[dt].split ? 2 : 1; }
 
 namespace {
 
@@ -442,6 +443,14 @@ extern "C" hb_status hubbard_autotune(hb_handle h, hb_dtype dt, const void *x, v
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return HB_ERR_CUDA;
+    }
+    if (h->ks) {  // momentum sectors have one launch shape: report its time
+        float ms = 0.f;
+        s = time_part(h, dt, x, y, st, kAll, reps, e0, e1, &ms);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (s == HB_OK && best) to_public(h->hv_cfg[dt], ms, best);
+        return s;
     }
     const HvConfig saved = h->hv_cfg[dt];
     HvConfig fused_win = saved, row_win = saved;

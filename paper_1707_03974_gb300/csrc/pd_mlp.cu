@@ -693,7 +693,7 @@ hb_status mlp_adam_step(hb_mlp_handle m, float lr, void *stream) {
 
 hb_status mlp_start_vector(hb_mlp_handle m, hb_handle h, hb_dtype dt, void *v, void *stream) {
     if (!m || !h || !v || (dt != HB_F64 && dt != HB_F32 && dt != HB_FX64)) return HB_ERR_INVALID_ARG;
-    if (2 * h->L != m->n_in) return HB_ERR_INVALID_ARG;
+    if (2 * h->L != m->n_in || h->ks) return HB_ERR_INVALID_ARG;  // real-space sites only
     hb_status s = pd_build_tables(h);
     if (s != HB_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

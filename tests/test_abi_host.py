@@ -56,8 +56,19 @@ def test_create_rejects_bad_arguments(lib, L, bonds, nu, nd):
     assert e.value.name == "HB_ERR_INVALID_ARG"
 
 
+@pytest.mark.parametrize("Lx,Ly,nu,nd,Kx,Ky", [(0, 1, 1, 1, 0, 0), (1, 1, 1, 1, 0, 0), (8, 5, 1, 1, 0, 0),
+                                                (4, 4, 17, 1, 0, 0), (4, 4, 1, -1, 0, 0), (4, 4, 1, 1, 4, 0),
+                                                (4, 4, 1, 1, 0, -1), (6, 1, 1, 1, 0, 1)])
+def test_create_k_rejects_bad_arguments(lib, Lx, Ly, nu, nd, Kx, Ky):
+    """Momentum-sector handles: grid of 2 .. 32 momenta, fillings and K inside the zone."""
+    with pytest.raises(pd.HubbardError) as e:
+        pd.Handle.momentum(Lx, Ly, 1.0, 0.0, 1.0, nu, nd, Kx, Ky)
+    assert e.value.name == "HB_ERR_INVALID_ARG"
+
+
 def test_null_pointer_arguments(lib):
     assert lib.hubbard_basis_create(4, 0, None, None, 1.0, 1, 1, None) == 1
+    assert lib.hubbard_basis_create_k(4, 4, 1.0, 0.0, 1.0, 1, 1, 0, 0, None) == 1
     assert lib.hubbard_basis_dim(None, None, None, None) == 1
     assert lib.hubbard_apply(None, 0, None, None, None) == 1
     assert lib.paradeisos_rank(None, None, None, 0, None) == 1
