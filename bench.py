@@ -38,6 +38,11 @@ WORKLOADS = {
     # smaller sector of the same cluster, for profiler captures (0.5 GB per vector, still > L2)
     "hubbard4x4_n6": {"workload": "hubbard_4x4_tp-0.3_U8_6up_6dn", "L": 16,
                       "lattice": "4x4 periodic, t=1, t'=-0.3", "U": 8.0, "N_up": 6, "N_dn": 6, "D": 64128064},
+    # one momentum sector of the benchmark cluster (Sec. IV A, Eq. 4): total momentum K = (0, 0)
+    "kspace4x4_K00": {"workload": "hubbard_4x4_tp-0.3_U8_half_filling_momentum_K00", "L": 16,
+                      "lattice": "4x4 periodic, t=1, t'=-0.3, momentum basis", "U": 8.0, "N_up": 8, "N_dn": 8,
+                      "K": [0, 0], "D": None,
+                      "l2": "83 MB per vector; a Lanczos step touches three (249 MB > L2), no flush"},
     # the precision workload: 18-site tilted cluster, run with --dtype f32 (float32 vectors)
     "tilted18_half": {"workload": "hubbard_18site_tilted_U6_half_filling", "L": 18,
                       "lattice": "18-site tilted square, lattice vectors (3,3), (3,-3), t=1", "U": 6.0,
@@ -196,10 +201,14 @@ def run_ours(args, world, rank, local):
     import workloads as wl
 
     dev = torch.device("cuda", local)
-    wk = WORKLOADS[args.workload]
+    wk = dict(WORKLOADS[args.workload])
     cl = wl.tilted_18() if wk["L"] == 18 else wl.square_periodic(4, 1.0, -0.3)
-    h = pd.Handle(cl.L, cl.bonds, cl.t, wk["U"], wk["N_up"], wk["N_dn"])
+    if "K" in wk:
+        h = pd.Handle.momentum(4, 4, 1.0, -0.3, wk["U"], wk["N_up"], wk["N_dn"], *wk["K"])
+    else:
+        h = pd.Handle(cl.L, cl.bonds, cl.t, wk["U"], wk["N_up"], wk["N_dn"])
     D = h.D
+    wk["D"] = D
     stream = torch.cuda.current_stream()
     # inputs: a normalised random start vector (plumbing, outside the timed region)
     g = torch.Generator(device=dev)
@@ -322,7 +331,7 @@ def run_ours(args, world, rank, local):
         del host_v
 
     solve = None
-    if not args.no_solve and rank == 0 and args.workload == "hubbard4x4_half":
+    if not args.no_solve and rank == 0 and args.workload in ("hubbard4x4_half", "kspace4x4_K00"):
         solve = time_to_e0(pd, h, torch)
     del V
     h.close()
@@ -348,7 +357,7 @@ def run_ours(args, world, rank, local):
                                    "H·v within 1e-12 of the float64 oracle, E0 within 1e-10 (tests)",
                            "f64": "IEEE float64 vectors and FMAs", "f32": "float32 vectors, float64 scalars"}[args.dtype],
         "data": "synthetic (seeded random start vector)",
-        "config": {**WORKLOADS[args.workload], **COMMON, "vector_dtype": args.dtype},
+        "config": {**COMMON, **wk, "vector_dtype": args.dtype},
         "hv_ms": round(hv_ms, 4), "hv_gstates_per_s": round(D / (hv_ms * 1e-3) / 1e9, 4),
         "hv_config": tuned,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

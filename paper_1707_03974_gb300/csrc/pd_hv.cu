@@ -356,6 +356,7 @@ hb_status apply_fx(hb_handle h, const int64_t *x, int64_t *y, cudaStream_t st, i
 }
 
 hb_status apply_part(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st, int part) {
+    if (h->ks) return pd_k_apply(h, dt, x, y, st);  // momentum sector: one kernel, no parts
     if (dt == HB_F64) return apply_t<double>(h, static_cast<const double *>(x), static_cast<double *>(y), st, part);
     if (dt == HB_FX64) return apply_fx(h, static_cast<const int64_t *>(x), static_cast<int64_t *>(y), st, part);
     return apply_t<float>(h, static_cast<const float *>(x), static_cast<float *>(y), st, part);

@@ -256,30 +256,33 @@ struct KHv {
     int Gun;
 };
 
-// One CTA per row (up string) at a time; thread j handles the row's j-th
+// One warp per row (up string) at a time; lane j handles the row's j-th
 // spin-down string.  y = diag x + (U/N) sum_q sum_{up move a} sum_{dn move b}
-// s_a s_b x[F_a + G_b].  Fixed point: the signed terms are summed exactly (two
-// non-negative running sums), then one rounded product each for the diagonal
-// and for U/N.
+// s_a s_b x[F_a + G_b], the up moves of the row staged in the warp's share of
+// shared memory, the gathers issued four at a time.  Fixed point: the signed
+// terms are summed exactly (two non-negative running sums), then one rounded
+// product each for the diagonal and for U/N.
 template <typename T>
 __global__ void __launch_bounds__(256) k_k_hv(KHv p, const T *__restrict__ x, T *__restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = p.a.N, nu = p.a.nu, nd = p.a.nd;
-    uint64_t *s_up = reinterpret_cast<uint64_t *>(smem);
-    uint8_t *s_cnt = reinterpret_cast<uint8_t *>(s_up + (size_t)(N - 1) * nu);
-    for (uint64_t r = blockIdx.x; r < p.Dup; r += gridDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const size_t per_warp = (size_t)(N - 1) * (nu > 0 ? nu : 1);
+    uint64_t *s_up = reinterpret_cast<uint64_t *>(smem) + warp * per_warp;
+    uint8_t *s_cnt = reinterpret_cast<uint8_t *>(reinterpret_cast<uint64_t *>(smem) + nwarps * per_warp) + warp * 32;
+    for (uint64_t r = (uint64_t)blockIdx.x * nwarps + warp; r < p.Dup; r += (uint64_t)gridDim.x * nwarps) {
         const int kd = (int)p.rowKd[r];
         const uint64_t len = p.doff[kd + 1] - p.doff[kd];
-        if (len == 0) continue;  // uniform across the CTA
-        __syncthreads();
-        for (int e = threadIdx.x; e < (N - 1) * nu; e += blockDim.x) s_up[e] = p.upmov[r * (uint64_t)(N - 1) * nu + e];
-        for (int e = threadIdx.x; e < N - 1; e += blockDim.x) s_cnt[e] = p.upcnt[r * (uint64_t)(N - 1) + e];
-        __syncthreads();
+        if (len == 0) continue;  // uniform across the warp
+        __syncwarp();
+        for (int e = lane; e < (N - 1) * nu; e += 32) s_up[e] = p.upmov[r * (uint64_t)(N - 1) * nu + e];
+        if (lane < N - 1) s_cnt[lane] = p.upcnt[r * (uint64_t)(N - 1) + lane];
+        __syncwarp();
         const uint64_t F = p.rowF[r], e0 = p.doff[kd];
         const double eur = p.eu[r];
         const uint32_t *dm = p.dnmov + p.mbase[kd];
         const uint8_t *dc = p.dncnt + p.cbase[kd];
-        for (uint64_t j = threadIdx.x; j < len; j += blockDim.x) {
+        for (uint64_t j = lane; j < len; j += 32) {
             const double diag = eur + p.ed[e0 + j] + p.U_diag;
             const T xI = x[F + j];
             int64_t pos = 0, neg = 0;
@@ -293,14 +296,22 @@ __global__ void __launch_bounds__(256) k_k_hv(KHv p, const T *__restrict__ x, T 
                     const uint32_t ev = dm[((uint64_t)(q - 1) * nd + b) * len + j];
                     const uint64_t G = ev & 0x7FFFFFFFu;
                     const uint64_t sb = ev >> 31;
-                    for (int aa = 0; aa < cu; ++aa) {
-                        const uint64_t m = ua[aa];
-                        const T v = x[(m & 0x7FFFFFFFFFFFFFFFull) + G];
-                        if constexpr (std::is_same<T, int64_t>::value) {
-                            if ((m >> 63) ^ sb) neg += v;
-                            else pos += v;
-                        } else {
-                            acc += ((m >> 63) ^ sb) ? -v : v;
+                    for (int a0 = 0; a0 < cu; a0 += 4) {
+                        uint64_t m[4];
+                        T v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            m[i] = a0 + i < cu ? ua[a0 + i] : 0;
+                            v[i] = a0 + i < cu ? x[(m[i] & 0x7FFFFFFFFFFFFFFFull) + G] : T(0);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if constexpr (std::is_same<T, int64_t>::value) {
+                                if ((m[i] >> 63) ^ sb) neg += v[i];
+                                else pos += v[i];
+                            } else {
+                                acc += ((m[i] >> 63) ^ sb) ? -v[i] : v[i];
+                            }
                         }
                     }
                 }
@@ -310,6 +321,90 @@ __global__ void __launch_bounds__(256) k_k_hv(KHv p, const T *__restrict__ x, T 
                 y[F + j] = fx_mul(xI, c.K, c.G) + fx_mul(pos - neg, p.Kun, p.Gun);
             } else {
                 y[F + j] = (T)diag * xI + (T)p.U_over_N * acc;
+            }
+        }
+    }
+}
+
+// Row-factorised form: for a row u and a momentum transfer q every up move
+// lands in a row of the same length (K_dn' = K_dn - q), so
+//     t_q = sum_a s_a x[row u'_a]
+// is formed once per (u, q) from whole rows read coalesced and kept in shared
+// memory, and each column j of row u then adds sum_b s_b t_q[G_b(j)], the
+// spin-down moves of its string gathered from shared memory (the same order of
+// work as the tensor-product H·v of Sec. II A).  One CTA per row; thread t
+// keeps the accumulators of columns t, t + blockDim, ... (JM of them).  In
+// fixed point every partial sum is an exact integer sum, so the result is the
+// same integer as the pairwise form's.
+template <typename T, int JM>
+__global__ void __launch_bounds__(256) k_k_hv_rows(KHv p, const T *__restrict__ x, T *__restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = p.a.N, nu = p.a.nu, nd = p.a.nd;
+    uint64_t *s_up = reinterpret_cast<uint64_t *>(smem);
+    const size_t nup = (size_t)(N - 1) * (nu > 0 ? nu : 1);
+    uint8_t *s_cnt = reinterpret_cast<uint8_t *>(s_up + nup);
+    T *s_t = reinterpret_cast<T *>(smem + ((nup * 8 + 32 + 15) & ~(size_t)15));
+    for (uint64_t r = blockIdx.x; r < p.Dup; r += gridDim.x) {
+        const int kd = (int)p.rowKd[r];
+        const uint64_t len = p.doff[kd + 1] - p.doff[kd];
+        if (len == 0) continue;  // uniform across the CTA
+        __syncthreads();
+        for (int e = threadIdx.x; e < (N - 1) * nu; e += blockDim.x) s_up[e] = p.upmov[r * (uint64_t)(N - 1) * nu + e];
+        if (threadIdx.x < N - 1) s_cnt[threadIdx.x] = p.upcnt[r * (uint64_t)(N - 1) + threadIdx.x];
+        __syncthreads();
+        const uint32_t *dm = p.dnmov + p.mbase[kd];
+        const uint8_t *dc = p.dncnt + p.cbase[kd];
+        int64_t acc_i[JM];
+        T acc_f[JM];
+#pragma unroll
+        for (int i = 0; i < JM; ++i) acc_i[i] = 0, acc_f[i] = T(0);
+        for (int q = 1; q < N; ++q) {
+            const int cu = s_cnt[q - 1];
+            if (cu == 0) continue;  // uniform
+            const int kd2 = ksub(p.a.Lx, p.a.Ly, kd, q);
+            const uint64_t len2 = p.doff[kd2 + 1] - p.doff[kd2];
+            const uint64_t *ua = s_up + (size_t)(q - 1) * nu;
+            __syncthreads();  // the previous q is done with s_t
+            for (uint64_t e = threadIdx.x; e < len2; e += blockDim.x) {
+                T t = T(0);
+                for (int a = 0; a < cu; ++a) {
+                    const uint64_t m = ua[a];
+                    const T v = x[(m & 0x7FFFFFFFFFFFFFFFull) + e];
+                    t = (m >> 63) ? t - v : t + v;
+                }
+                s_t[e] = t;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < JM; ++i) {
+                const uint64_t j = threadIdx.x + (uint64_t)i * blockDim.x;
+                if (j >= len) break;
+                const int cd = dc[(uint64_t)(q - 1) * len + j];
+                for (int b = 0; b < cd; ++b) {
+                    const uint32_t ev = dm[((uint64_t)(q - 1) * nd + b) * len + j];
+                    const T v = s_t[ev & 0x7FFFFFFFu];
+                    if constexpr (std::is_same<T, int64_t>::value) {
+                        const int64_t mneg = -(int64_t)(ev >> 31);
+                        acc_i[i] += (v ^ mneg) - mneg;
+                    } else {
+                        acc_f[i] += (ev >> 31) ? -v : v;
+                    }
+                }
+            }
+        }
+        const uint64_t F = p.rowF[r], e0 = p.doff[kd];
+        const double eur = p.eu[r];
+#pragma unroll
+        for (int i = 0; i < JM; ++i) {
+            const uint64_t j = threadIdx.x + (uint64_t)i * blockDim.x;
+            if (j >= len) break;
+            const double diag = eur + p.ed[e0 + j] + p.U_diag;
+            const T xI = x[F + j];
+            if constexpr (std::is_same<T, int64_t>::value) {
+                const FxCoef c = fx_coef_dev(diag);
+                y[F + j] = fx_mul(xI, c.K, c.G) + fx_mul(acc_i[i], p.Kun, p.Gun);
+            } else {
+                y[F + j] = (T)diag * xI + (T)p.U_over_N * acc_f[i];
             }
         }
     }
@@ -557,18 +652,46 @@ hb_status build_kspace(hb_handle h, KSpace &k) {
 
 }  // namespace
 
-hb_status pd_k_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st) {
-    const KHv p = khv(h);
-    const size_t smem = (size_t)(h->ks->N - 1) * std::max(h->ks->nu, 1) * 8 + h->ks->N;
-    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(h->ks->Dup, (uint64_t)h->sm_count * 8));
-    if (dt == HB_F64)
-        k_k_hv<double><<<grid, 256, smem, st>>>(p, static_cast<const double *>(x), static_cast<double *>(y));
-    else if (dt == HB_F32)
-        k_k_hv<float><<<grid, 256, smem, st>>>(p, static_cast<const float *>(x), static_cast<float *>(y));
-    else
-        k_k_hv<int64_t><<<grid, 256, smem, st>>>(p, static_cast<const int64_t *>(x), static_cast<int64_t *>(y));
+namespace {
+
+template <typename T, int JM>
+hb_status launch_rows(hb_handle h, const KHv &p, const T *x, T *y, cudaStream_t st, uint64_t maxlen) {
+    const size_t nup = (size_t)(h->ks->N - 1) * std::max(h->ks->nu, 1);
+    const size_t smem = ((nup * 8 + 32 + 15) & ~(size_t)15) + (size_t)maxlen * sizeof(T);
+    auto kern = k_k_hv_rows<T, JM>;
+    PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+    if (per_sm < 1) return HB_ERR_NO_MEMORY;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(h->ks->Dup, (uint64_t)per_sm * h->sm_count));
+    kern<<<grid, 256, smem, st>>>(p, x, y);
     PD_CUDA(cudaGetLastError());
     return HB_OK;
+}
+
+template <typename T>
+hb_status k_apply_t(hb_handle h, const T *x, T *y, cudaStream_t st) {
+    const KHv p = khv(h);
+    uint64_t maxlen = 0;
+    for (int k = 0; k < h->ks->N; ++k) maxlen = std::max(maxlen, h->ks->h_doff[k + 1] - h->ks->h_doff[k]);
+    // row-factorised form while a row fits the per-thread accumulators and shared memory
+    if (maxlen <= 4 * 256 && maxlen * sizeof(T) <= 96 * 1024) return launch_rows<T, 4>(h, p, x, y, st, maxlen);
+    if (maxlen <= 16 * 256 && maxlen * sizeof(T) <= 96 * 1024) return launch_rows<T, 16>(h, p, x, y, st, maxlen);
+    constexpr int kWarps = 8;  // pairwise form, one row per warp
+    const size_t smem = (size_t)kWarps * ((size_t)(h->ks->N - 1) * std::max(h->ks->nu, 1) * 8 + 32);
+    const unsigned grid =
+        (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((h->ks->Dup + kWarps - 1) / kWarps, (uint64_t)h->sm_count * 8));
+    k_k_hv<T><<<grid, 256, smem, st>>>(p, x, y);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+}  // namespace
+
+hb_status pd_k_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st) {
+    if (dt == HB_F64) return k_apply_t<double>(h, static_cast<const double *>(x), static_cast<double *>(y), st);
+    if (dt == HB_F32) return k_apply_t<float>(h, static_cast<const float *>(x), static_cast<float *>(y), st);
+    return k_apply_t<int64_t>(h, static_cast<const int64_t *>(x), static_cast<int64_t *>(y), st);
 }
 
 hb_status pd_k_rank(hb_handle h, const uint64_t *states, uint64_t *idx, uint64_t n, cudaStream_t st) {

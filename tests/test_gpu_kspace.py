@@ -132,3 +132,31 @@ def test_square4x4_half_filling_sectors(env):
         h.close()
     assert D == 12870 ** 2
     assert abs(min(E) - gold) <= 1e-10 * max(1.0, abs(gold))
+
+
+def test_autotune_and_step_on_a_sector(env):
+    """The configuration and stepping entry points accept a momentum handle (its H·v has one
+    launch shape: autotune only times it) and give the same vector as hubbard_apply."""
+    import ctypes
+    torch, pd = env
+    h = pd.Handle.momentum(3, 3, 1.0, -0.3, 5.0, 2, 2, 1, 2)
+    x = torch.rand(h.D, dtype=torch.float64, device="cuda") - 0.5
+    x /= x.norm()
+    ref = pd.hubbard_apply(h, x).clone()
+    y = torch.empty_like(x)
+    best = pd.hubbard_autotune(h, x, y, reps=2)
+    assert best["ms"] > 0
+    assert torch.equal(pd.hubbard_apply(h, x), ref)
+    scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device="cuda")
+    a = torch.zeros(1, dtype=torch.float64, device="cuda")
+    b = torch.zeros(1, dtype=torch.float64, device="cuda")
+    w = torch.empty_like(x)
+    n = ctypes.c_uint32(0)
+    pd.lanczos_step(h, x, None, w, None, a, b, scratch, launches=n)
+    torch.cuda.synchronize()
+    assert n.value == 1 + 5
+    alpha = float(torch.dot(ref, x))
+    assert abs(a.item() - alpha) < 1e-12
+    assert torch.allclose(w * b.item(), ref - alpha * x, atol=1e-12)
+    assert pd.hubbard_last_error(h) == "HB_OK"
+    h.close()
