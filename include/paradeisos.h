@@ -336,6 +336,32 @@ hb_status lanczos_batch_workspace_bytes(hb_batch_handle b, const hb_lanczos_opts
 hb_status lanczos_batch_ground_state(hb_batch_handle b, const hb_lanczos_opts *opts, void *workspace,
                                      uint64_t workspace_bytes, double *E0, hb_lanczos_info *info, void *stream);
 
+/* ---------------- inversion-symmetric maps (Sec. IV B) ---------------- */
+
+/*
+ * Index maps of the inversion-symmetric subspace of n particles on an N-site
+ * chain (F maps site i to N-1-i): one basis element per orbit {phi, F(phi)},
+ * ordered by the classification tree of Sec. IV B (outermost unclassified bit
+ * pair (N-1-d, d): class A (0,1) is a leaf ranked by the forward map of Eq. 3 on
+ * its inner bits, class B (0,0) and class C (1,1) recurse; A before B before C;
+ * subtree sizes S_i^m = C_{i-2}^{m-1} + S_{i-2}^m + S_{i-2}^{m-2}).
+ * 1 <= N <= 32, 0 <= n <= N.  The handle owns two small tables on the current device.
+ */
+typedef struct hb_inv *hb_inv_handle;
+hb_status paradeisos_inv_create(int N, int n, hb_inv_handle *out);
+hb_status paradeisos_inv_destroy(hb_inv_handle h);
+/* D = number of orbits = (C(N,n) + number of palindromes) / 2 */
+hb_status paradeisos_inv_dim(hb_inv_handle h, uint64_t *D);
+/* Orbit index of each string (either member of an orbit gives the same index).
+ * A string with bits >= N or a popcount != n gives UINT64_MAX and the sticky
+ * HB_ERR_INVALID_STATE.  states, idx: device [n_items]; asynchronous on stream. */
+hb_status paradeisos_inv_rank(hb_inv_handle h, const uint64_t *states, uint64_t *idx, uint64_t n_items, void *stream);
+/* Representative of each index (the member whose first unequal outer pair reads (0,1),
+ * or the palindrome); an index >= D gives UINT64_MAX and HB_ERR_OUT_OF_RANGE. */
+hb_status paradeisos_inv_unrank(hb_inv_handle h, const uint64_t *idx, uint64_t *states, uint64_t n_items, void *stream);
+/* Sticky error of the handle (synchronises the device, returns and clears it). */
+hb_status paradeisos_inv_last_error(hb_inv_handle h);
+
 /*
  * Host utility (no GPU needed): lowest eigenvalue theta of the symmetric
  * tridiagonal matrix with diagonal alpha[0..n) and off-diagonal beta[0..n-1),

@@ -5,7 +5,7 @@ the C ABI of include/paradeisos.h); this package is its thin ctypes binding.
 Importing the package does not load the library; the first call does, and fails
 loudly if the library has not been built.
 """
-from ._binding import (HB_F32, HB_F64, HB_FX64, Batch, Handle, Mlp, mlp_adam_step, mlp_forward, mlp_gradient,
+from ._binding import (HB_F32, HB_F64, HB_FX64, Batch, Handle, Inversion, Mlp, mlp_adam_step, mlp_forward, mlp_gradient,
                        mlp_last_error, mlp_start_vector, mlp_tc_gemm, hb_device_wait_selftest, hubbard_autotune, hubbard_batch_apply,
                        hubbard_batch_autotune, lanczos_batch_ground_state, hubbard_convert,
                        hubbard_fixed_point_bits, hubbard_get_hv_config, hubbard_set_hv_config, HubbardError, LanczosResult, hb_tridiag_lowest,  # noqa: F401
@@ -21,7 +21,9 @@ EXPORTED_SYMBOLS = ("hb_status_string", "hubbard_basis_create", "hubbard_basis_c
                     "hubbard_fixed_point_bits", "hubbard_convert", "hubbard_get_hv_config",
                     "hubbard_set_hv_config", "hubbard_autotune", "lanczos_ritz_vector_f32", "hubbard_batch_create", "hubbard_batch_destroy",
                     "hubbard_batch_layout", "hubbard_batch_apply", "hubbard_batch_autotune",
-                    "lanczos_batch_workspace_bytes", "lanczos_batch_ground_state")
+                    "lanczos_batch_workspace_bytes", "lanczos_batch_ground_state", "paradeisos_inv_create",
+                    "paradeisos_inv_destroy", "paradeisos_inv_dim", "paradeisos_inv_rank", "paradeisos_inv_unrank",
+                    "paradeisos_inv_last_error")
 MLP_SYMBOLS = ("mlp_create", "mlp_destroy", "mlp_param_count", "mlp_get_params", "mlp_set_params", "mlp_forward",
                "mlp_gradient", "mlp_adam_step", "mlp_start_vector", "mlp_last_error", "mlp_tc_gemm",
                "hb_device_wait_selftest")

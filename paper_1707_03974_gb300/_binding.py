@@ -79,6 +79,12 @@ def load():
         "lanczos_ground_state": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, P, U64, P, P,
                                                 ctypes.POINTER(D), ctypes.POINTER(LanczosInfo), P]),
         "hb_tridiag_lowest": (ctypes.c_int, [P, P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "paradeisos_inv_create": (ctypes.c_int, [I32, I32, ctypes.POINTER(P)]),
+        "paradeisos_inv_destroy": (ctypes.c_int, [P]),
+        "paradeisos_inv_dim": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64)]),
+        "paradeisos_inv_rank": (ctypes.c_int, [P, P, P, ctypes.c_uint64, P]),
+        "paradeisos_inv_unrank": (ctypes.c_int, [P, P, P, ctypes.c_uint64, P]),
+        "paradeisos_inv_last_error": (ctypes.c_int, [P]),
         "hubbard_fixed_point_bits": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "lanczos_ritz_vector_f32": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, P, U64, P,
                                                    ctypes.POINTER(D), ctypes.POINTER(LanczosInfo), P]),
@@ -606,3 +612,45 @@ def mlp_tc_gemm(A, B, stream=None):
     C = torch.empty((M, N), dtype=torch.float32, device=A.device)
     _check(load().mlp_tc_gemm(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), _stream_ptr(stream)), "mlp_tc_gemm")
     return C
+
+
+class Inversion:
+    """Inversion-symmetric maps of n particles on an N-site chain (paradeisos_inv_*)."""
+
+    def __init__(self, N: int, n: int):
+        h = ctypes.c_void_p()
+        _check(load().paradeisos_inv_create(int(N), int(n), ctypes.byref(h)), "paradeisos_inv_create")
+        self._h, self.N, self.n = h, int(N), int(n)
+        D = ctypes.c_uint64()
+        _check(load().paradeisos_inv_dim(h, ctypes.byref(D)), "paradeisos_inv_dim")
+        self.D = D.value
+
+    def rank(self, states, stream=None):
+        import torch
+        _need_cuda(states)
+        out = torch.empty_like(states)
+        _check(load().paradeisos_inv_rank(self._h, _ptr(states), _ptr(out), states.numel(), _stream_ptr(stream)),
+               "paradeisos_inv_rank")
+        return out
+
+    def unrank(self, idx, stream=None):
+        import torch
+        _need_cuda(idx)
+        out = torch.empty_like(idx)
+        _check(load().paradeisos_inv_unrank(self._h, _ptr(idx), _ptr(out), idx.numel(), _stream_ptr(stream)),
+               "paradeisos_inv_unrank")
+        return out
+
+    def last_error(self) -> str:
+        return STATUS[load().paradeisos_inv_last_error(self._h)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().paradeisos_inv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
