@@ -17,7 +17,11 @@ Definitions used (each function cites the passage it follows):
   textbook Lanczos iteration (which the paper cites but does not specify);
 * the momentum-space sectors (Sec. IV A, ``momentum.py``) are ascending lists of
   (up, dn) strings over the single-particle momenta with fixed total momentum,
-  and their Hamiltonian is Eq. 4 term by term.
+  and their Hamiltonian is Eq. 4 term by term;
+* the inversion-symmetric maps (Sec. IV B, ``inversion.py``) follow the
+  classification tree; the single-particle Green's function (``response.py``)
+  is the spectral sum over a dense target sector and the continued fraction of
+  a textbook Lanczos run.
 
 Parity status: every function here is pinned by tests against values printed in
 the paper or fixed by mathematics (closed forms, invariants, brute force), except
