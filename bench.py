@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="hubbard4x4_half",
-                   choices=sorted(WORKLOADS) + ["batch64", "learned4x4", "start4x4"])
+                   choices=sorted(WORKLOADS) + ["batch64", "learned4x4", "start4x4", "green4x4"])
     p.add_argument("--dtype", default="fx64", choices=["f64", "fx64", "f32"],
                    help="Krylov vector type: fixed-point int64 (default, float64-grade accuracy without the "
                         "float64 pipe), float64 (float64 FMAs), float32")
@@ -653,12 +653,54 @@ def run_start(args, world, rank, local):
     h.close()
 
 
+def run_green(args, world, rank, local):
+    """Single-particle spectral function of the 4x4 t-t' ground state (U = 8, half filling, K = (0,0))
+    by the Lanczos continued fraction: float64 ground state, then for k = (0,0), (pi/2,pi/2), (pi,0)
+    the removal and addition parts (spin up), 200 Lanczos steps each."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1707_03974_gb300.build import build
+    build()
+    import paper_1707_03974_gb300 as pd
+    from paper_1707_03974_gb300 import response
+    h = pd.Handle.momentum(4, 4, 1.0, -0.3, 8.0, 8, 8, 0, 0)
+    z = np.linspace(-12.0, 12.0, 481) + 0.1j
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gs = response.ground(h)
+    torch.cuda.synchronize()
+    t_ground = time.perf_counter() - t0
+    parts = {}
+    t1 = time.perf_counter()
+    for name, k in (("k00", 0), ("kpi2pi2", 5), ("kpi0", 2)):
+        for part in ("removal", "addition"):
+            G, info = response.green(gs, k, 0, part, z, steps=200)
+            parts[f"{name}_{part}"] = {"seconds": round(info["seconds"], 4), "weight": round(info["norm2"], 6),
+                                       "D_target": info["D_target"], "steps": info["steps"],
+                                       "peak_omega": float(z.real[int(np.argmax(-G.imag))])}
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t1
+    out = {"metric": "spectral function A(k, omega): seconds for 3 momenta x (removal + addition), 200 Lanczos steps each",
+           "value": round(t_all, 4), "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (the method's own ground state)",
+           "config": {"workload": "green_function_4x4_tp-0.3_U8_half_filling_K00", "D_ground_sector": h.D,
+                      "eta": 0.1, "omega_points": len(z)},
+           "ground_state_seconds": round(t_ground, 4), "E0": gs.E0, "parts": parts}
+    print(json.dumps(out))
+    h.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.workload == "learned4x4" and args.impl == "ours":
         if rank == 0:
             run_learned(args, world, rank, local)
+        return
+    if args.workload == "green4x4" and args.impl == "ours":
+        if rank == 0:
+            run_green(args, world, rank, local)
         return
     if args.workload == "start4x4" and args.impl == "ours":
         if rank == 0:

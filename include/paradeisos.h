@@ -336,6 +336,41 @@ hb_status lanczos_batch_workspace_bytes(hb_batch_handle b, const hb_lanczos_opts
 hb_status lanczos_batch_ground_state(hb_batch_handle b, const hb_lanczos_opts *opts, void *workspace,
                                      uint64_t workspace_bytes, double *E0, hb_lanczos_info *info, void *stream);
 
+/* ---------------- dynamical response (the continued fraction named in Sec. I) ---------------- */
+
+/*
+ * float64 Lanczos (three-term recurrence) to opts->tol, then the normalised
+ * float64 Ritz vector of E0 in ritz (device double[D]), rebuilt by replaying the
+ * recurrence from a stored copy of the start vector with the recorded alpha,
+ * beta.  Workspace: lanczos_workspace_bytes for vec_dtype HB_F64 (reorth 0)
+ * plus 8 D bytes rounded up to a multiple of 256.  Synchronises `stream`.
+ */
+hb_status lanczos_ritz_vector_f64(hb_handle h, const hb_lanczos_opts *opts, const void *v0, void *workspace,
+                                  uint64_t workspace_bytes, double *ritz, double *E0, hb_lanczos_info *info,
+                                  void *stream);
+
+/*
+ * y = c_{k s} x (op 0) or y = c+_{k s} x (op 1) between two momentum-sector
+ * handles of the same cluster (hubbard_basis_create_k): dst must be the sector
+ * with one particle of spin s (0 up, 1 down) fewer (more) and total momentum
+ * K - k_k (K + k_k).  Sign convention: the many-body state is the up creators in
+ * descending momentum index followed by the down creators, so the operator
+ * carries (-1)^(particles of spin s above bit k), times (-1)^(N_up) for s = down.
+ * x: device vector of the source sector, y of the target (dt HB_F64 or HB_F32).
+ * norm2: optional device double receiving ||y||^2.  Asynchronous on `stream`.
+ */
+hb_status hubbard_apply_c(hb_handle src, hb_handle dst, int op, int spin, int k, hb_dtype dt, const void *x, void *y,
+                          double *norm2, void *stream);
+
+/*
+ * Host utility: the Lanczos continued fraction
+ *   G(z) = norm2 / (z + E0 - alpha_0 - beta_0^2 / (z + E0 - alpha_1 - ... - beta_{n-2}^2 / (z + E0 - alpha_{n-1})))
+ * at nz complex points z = z_re + i z_im (alpha[n], beta[n-1] from a Lanczos run
+ * started at phi / ||phi||, norm2 = ||phi||^2).
+ */
+hb_status hb_continued_fraction(const double *alpha, const double *beta, int n, double norm2, double E0,
+                                const double *z_re, const double *z_im, int nz, double *g_re, double *g_im);
+
 /* ---------------- inversion-symmetric maps (Sec. IV B) ---------------- */
 
 /*

@@ -80,6 +80,10 @@ def load():
                                                 ctypes.POINTER(D), ctypes.POINTER(LanczosInfo), P]),
         "hb_tridiag_lowest": (ctypes.c_int, [P, P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "paradeisos_inv_create": (ctypes.c_int, [I32, I32, ctypes.POINTER(P)]),
+        "lanczos_ritz_vector_f64": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, P, U64, P, ctypes.POINTER(D),
+                                                   ctypes.POINTER(LanczosInfo), P]),
+        "hubbard_apply_c": (ctypes.c_int, [P, P, I32, I32, I32, I32, P, P, P, P]),
+        "hb_continued_fraction": (ctypes.c_int, [P, P, I32, D, D, P, P, I32, P, P]),
         "paradeisos_inv_destroy": (ctypes.c_int, [P]),
         "paradeisos_inv_dim": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64)]),
         "paradeisos_inv_rank": (ctypes.c_int, [P, P, P, ctypes.c_uint64, P]),
@@ -173,6 +177,7 @@ class Handle:
         self.L, self.N_up, self.N_dn, self.U = int(Lx * Ly), int(N_up), int(N_dn), float(U)
         self.n_bonds = 0
         self.Lx, self.Ly, self.K = int(Lx), int(Ly), (int(Kx), int(Ky))
+        self.t, self.tp = float(t), float(tp)
         D, Du, Dd = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(lib.hubbard_basis_dim(h, ctypes.byref(D), ctypes.byref(Du), ctypes.byref(Dd)), "hubbard_basis_dim")
         self.D, self.D_up, self.D_dn = D.value, Du.value, Dd.value
@@ -654,3 +659,51 @@ class Inversion:
             self.close()
         except Exception:
             pass
+
+
+def lanczos_ritz_vector_f64(h: Handle, maxit: int = 3000, tol: float = 1e-10, seed: int = 0, v0=None,
+                            check_every: int = 10, stream=None):
+    """(E0, normalised float64 Ritz vector of E0, LanczosInfo) by float64 Lanczos and the replayed recurrence."""
+    import torch
+    lib = load()
+    o = LanczosOpts(int(maxit), 0, HB_F64, int(check_every), float(tol), int(seed) & ((1 << 64) - 1), 0, 0)
+    nb = ctypes.c_uint64()
+    _check(lib.lanczos_workspace_bytes(h.ptr, ctypes.byref(o), ctypes.byref(nb)), "lanczos_workspace_bytes")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    extra = (h.D * 8 + 255) // 256 * 256
+    ws = torch.empty(nb.value + extra, dtype=torch.uint8, device=dev)
+    ritz = torch.empty(h.D, dtype=torch.float64, device=dev)
+    E0 = ctypes.c_double()
+    info = LanczosInfo()
+    st = lib.lanczos_ritz_vector_f64(h.ptr, ctypes.byref(o), _ptr(v0) if v0 is not None else None, _ptr(ws),
+                                     ws.numel(), _ptr(ritz), ctypes.byref(E0), ctypes.byref(info),
+                                     _stream_ptr(stream))
+    if st not in (0, 7):  # HB_OK, HB_ERR_NOT_CONVERGED
+        _check(st, "lanczos_ritz_vector_f64")
+    return E0.value, ritz, info
+
+
+def hubbard_apply_c(src: Handle, dst: Handle, op: str, spin: int, k: int, x, stream=None):
+    """y = c_{k spin} x (op 'c') or c+_{k spin} x (op 'cdag') between momentum sectors; returns (y, ||y||^2)."""
+    import torch
+    _need_cuda(x)
+    y = torch.empty(dst.D, dtype=x.dtype, device=x.device)
+    n2 = torch.zeros(1, dtype=torch.float64, device=x.device)
+    _check(load().hubbard_apply_c(src.ptr, dst.ptr, {"c": 0, "cdag": 1}[op], int(spin), int(k), _dtype_code(x),
+                                  _ptr(x), _ptr(y), _ptr(n2), _stream_ptr(stream)), "hubbard_apply_c")
+    return y, n2
+
+
+def hb_continued_fraction(alphas, betas, norm2: float, E0: float, z):
+    """G(z) of the Lanczos continued fraction at the complex points z (host utility)."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+    z = np.asarray(z, dtype=complex).ravel()
+    zr, zi = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+    gr, gi = np.empty(len(z)), np.empty(len(z))
+    P = ctypes.c_void_p
+    _check(load().hb_continued_fraction(P(a.ctypes.data), P(b.ctypes.data) if len(b) else None, len(a),
+                                        float(norm2), float(E0), P(zr.ctypes.data), P(zi.ctypes.data), len(z),
+                                        P(gr.ctypes.data), P(gi.ctypes.data)), "hb_continued_fraction")
+    return gr + 1j * gi

@@ -774,3 +774,68 @@ extern "C" hb_status hubbard_basis_create_k(int Lx, int Ly, double t, double tp,
     *out = h;
     return HB_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Single-particle operators between momentum sectors (for the continued-
+// fraction Green's function): y = c_{k s} x (op 0) or c+_{k s} x (op 1).  With
+// the up creators (descending momentum index) to the left of the down
+// creators, both carry (-1)^(particles of spin s above bit k) and, for s = down,
+// (-1)^(N_up).  One thread per target state: its source state differs in bit k
+// of spin s; the norm^2 of y is accumulated into *norm2 (if given).
+
+namespace {
+
+template <typename T>
+__global__ void k_k_apply_c(KArgs src, KArgs dst, uint64_t Ddst, int op, int spin, int k, const T *__restrict__ x,
+                            T *__restrict__ y, double *norm2) {
+    double acc = 0.0;
+    for (uint64_t J = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; J < Ddst; J += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = 0, d = 0;
+        kbwd_spin(dst, J, &u, &d);
+        const uint32_t part = spin == 0 ? u : d;
+        const uint32_t has = (part >> k) & 1u;
+        T v = T(0);
+        // annihilation: the target lacks k, the source has it; creation: the reverse
+        if ((op == 0 && !has) || (op == 1 && has)) {
+            const uint32_t p2 = part ^ (1u << k);
+            const uint32_t us = spin == 0 ? p2 : u, ds = spin == 0 ? d : p2;
+            int kd = 0;
+            const uint32_t g = kfwd_dn(src, ds, &kd);
+            const uint64_t I = kfwd_up(src, us, kd) + g;
+            int sgn = __popc(p2 >> (k + 1)) & 1;
+            if (spin == 1) sgn ^= __popc(us) & 1;
+            v = sgn ? -x[I] : x[I];
+        }
+        y[J] = v;
+        acc += (double)v * (double)v;
+    }
+    if (norm2) {
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(norm2, acc);
+    }
+}
+
+}  // namespace
+
+extern "C" hb_status hubbard_apply_c(hb_handle src, hb_handle dst, int op, int spin, int k, hb_dtype dt,
+                                     const void *x, void *y, double *norm2, void *stream) {
+    if (!src || !dst || !x || !y || !src->ks || !dst->ks || (op != 0 && op != 1) || (spin != 0 && spin != 1))
+        return HB_ERR_INVALID_ARG;
+    if (dt != HB_F64 && dt != HB_F32) return HB_ERR_INVALID_ARG;
+    const KSpace &a = *src->ks, &b = *dst->ks;
+    if (a.Lx != b.Lx || a.Ly != b.Ly || k < 0 || k >= a.N) return HB_ERR_INVALID_ARG;
+    const int dn_ = op == 0 ? -1 : 1;
+    const int want_nu = a.nu + (spin == 0 ? dn_ : 0), want_nd = a.nd + (spin == 1 ? dn_ : 0);
+    const int want_K = op == 0 ? ksub(a.Lx, a.Ly, a.K, k) : kadd(a.Lx, a.Ly, a.K, k);
+    if (b.nu != want_nu || b.nd != want_nd || b.K != want_K) return HB_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (norm2) PD_CUDA(cudaMemsetAsync(norm2, 0, sizeof(double), st));
+    if (dt == HB_F64)
+        k_k_apply_c<double><<<grid_for(dst->D, dst->sm_count), kThreads, 0, st>>>(
+            kargs(a), kargs(b), dst->D, op, spin, k, static_cast<const double *>(x), static_cast<double *>(y), norm2);
+    else
+        k_k_apply_c<float><<<grid_for(dst->D, dst->sm_count), kThreads, 0, st>>>(
+            kargs(a), kargs(b), dst->D, op, spin, k, static_cast<const float *>(x), static_cast<float *>(y), norm2);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}

@@ -15,6 +15,7 @@
 // per-thread values are then combined in a fixed tree order (deterministic).
 #include <algorithm>
 #include <chrono>
+#include <complex>
 #include <cfloat>
 #include <cmath>
 #include <type_traits>
@@ -861,9 +862,68 @@ hb_status replay_ritz_f32(Solve &s, const PhaseResult &r, float *start_copy, flo
     return HB_OK;
 }
 
+// Ritz vector of float64 Lanczos: the same replay in float64 (the regeneration
+// repeats the float64 step's operations: w - beta_prev vprev, - alpha v, * (1/beta))
+__global__ void k_axpy_scalar_f64(double *__restrict__ y, const double *__restrict__ v, double c, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        y[i] += c * v[i];
+}
+
+__global__ void k_regen_f64(double *__restrict__ w, const double *__restrict__ v, const double *__restrict__ vprev,
+                            double al, double bp, double inv_b, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        double wi = w[i];
+        if (vprev) wi = wi - bp * vprev[i];
+        wi = wi - al * v[i];
+        w[i] = wi * inv_b;
+    }
+}
+
+hb_status replay_ritz_f64(Solve &s, const PhaseResult &r, double *start_copy, double *V, uint64_t stride) {
+    const uint64_t D = s.D;
+    const int m = r.iters;
+    std::vector<double> svec;
+    double th, sl;
+    tridiag_lowest_host(r.alpha.data(), r.beta.data(), m, &th, &sl, &svec);
+    double *y = V;
+    double *a = V + 1 * stride, *b = V + 2 * stride;
+    double *vj = start_copy, *vp = nullptr, *wbuf = a, *spare = b;
+    PD_CUDA(cudaMemsetAsync(y, 0, D * 8, s.st));
+    for (int k = 0; k < m; ++k) {
+        k_axpy_scalar_f64<<<s.grid_vec, kRedThreads, 0, s.st>>>(y, vj, svec[k], D);
+        if (k + 1 == m) break;
+        hb_status st = pd_apply(s.h, HB_F64, vj, wbuf, s.st);
+        if (st != HB_OK) return st;
+        const double bk = r.beta[k];
+        k_regen_f64<<<s.grid_vec, kRedThreads, 0, s.st>>>(wbuf, vj, vp, r.alpha[k], k > 0 ? r.beta[k - 1] : 0.0,
+                                                          bk != 0 ? 1.0 / bk : 0.0, D);
+        double *old_vp = vp ? vp : spare;
+        vp = vj;
+        vj = wbuf;
+        wbuf = old_vp;
+    }
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+hb_status hb_continued_fraction(const double *alpha, const double *beta, int n, double norm2, double E0,
+                                const double *z_re, const double *z_im, int nz, double *g_re, double *g_im) {
+    if (!alpha || n < 1 || (n > 1 && !beta) || nz < 0 || (nz > 0 && (!z_re || !z_im || !g_re || !g_im)))
+        return HB_ERR_INVALID_ARG;
+    for (int q = 0; q < nz; ++q) {
+        const std::complex<double> z(z_re[q] + E0, z_im[q]);
+        std::complex<double> g = z - alpha[n - 1];
+        for (int j = n - 2; j >= 0; --j) g = z - alpha[j] - beta[j] * beta[j] / g;
+        const std::complex<double> G = norm2 / g;
+        g_re[q] = G.real();
+        g_im[q] = G.imag();
+    }
+    return HB_OK;
+}
 
 hb_status hb_tridiag_lowest(const double *alpha, const double *beta, int n, double *theta, double *s_last) {
     if (!alpha || n < 1 || (n > 1 && !beta) || !theta || !s_last) return HB_ERR_INVALID_ARG;
@@ -1089,6 +1149,61 @@ hb_status lanczos_ritz_vector_f32(hb_handle h, const hb_lanczos_opts *o, const v
         info->residual = r.res;
         info->iterations = r.iters;
         info->iterations_f32 = r.iters;
+        info->status = r.converged ? HB_OK : HB_ERR_NOT_CONVERGED;
+        info->converged = r.converged;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return r.converged ? HB_OK : HB_ERR_NOT_CONVERGED;
+}
+
+hb_status lanczos_ritz_vector_f64(hb_handle h, const hb_lanczos_opts *o, const void *v0, void *workspace,
+                                  uint64_t workspace_bytes, double *ritz, double *E0, hb_lanczos_info *info,
+                                  void *stream) {
+    if (!h || !o || !workspace || !ritz || !E0 || o->maxit < 1 || o->check_every < 1 || o->reorth)
+        return HB_ERR_INVALID_ARG;
+    hb_lanczos_opts oo = *o;
+    oo.vec_dtype = HB_F64;
+    oo.fp64_finish = 0;
+    const Layout L = make_layout(h, oo);
+    const uint64_t D = h->D, stride = align256(D * 8) / 8;
+    if (workspace_bytes < L.total + align256(D * 8)) return HB_ERR_NO_MEMORY;
+    if ((uintptr_t)workspace % 256 != 0) return HB_ERR_INVALID_ARG;
+    hb_status st = pd_build_tables(h);
+    if (st != HB_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    char *ws = static_cast<char *>(workspace);
+    Solve s;
+    s.h = h;
+    s.st = reinterpret_cast<cudaStream_t>(stream);
+    s.D = D;
+    s.nblk = L.nblk;
+    s.partials = reinterpret_cast<double *>(ws + L.partials);
+    s.d_alpha = reinterpret_cast<double *>(ws + L.scal);
+    s.d_beta = s.d_alpha + (oo.maxit + 1);
+    s.d_coef = s.d_beta + (oo.maxit + 1);
+    s.d_misc = s.d_coef + (oo.maxit + 1);
+    s.grid_vec = h->sm_count * 8;
+    double *V = reinterpret_cast<double *>(ws + L.vec);
+    double *start_copy = reinterpret_cast<double *>(ws + L.total);
+    if (v0)
+        k_copy<double><<<s.grid_vec, kRedThreads, 0, s.st>>>(static_cast<const double *>(v0), V, D);
+    else
+        k_fill_random<double><<<s.grid_vec, kRedThreads, 0, s.st>>>(V, D, oo.seed);
+    if ((st = normalise(s, V)) != HB_OK) return st;
+    k_copy<double><<<s.grid_vec, kRedThreads, 0, s.st>>>(V, start_copy, D);
+    PhaseResult r;
+    st = lanczos_run<double>(s, HB_F64, V, stride, oo.maxit, false, oo.tol, oo.check_every, r);
+    if (st != HB_OK) return st;
+    if ((st = replay_ritz_f64(s, r, start_copy, V, stride)) != HB_OK) return st;
+    if ((st = normalise(s, V)) != HB_OK) return st;
+    k_copy<double><<<s.grid_vec, kRedThreads, 0, s.st>>>(V, ritz, D);
+    PD_CUDA(cudaStreamSynchronize(s.st));
+    *E0 = r.theta;
+    if (info) {
+        info->E0 = r.theta;
+        info->residual = r.res;
+        info->iterations = r.iters;
+        info->iterations_f32 = 0;
         info->status = r.converged ? HB_OK : HB_ERR_NOT_CONVERGED;
         info->converged = r.converged;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -98,3 +98,16 @@ def test_tridiag_lowest_lanczos_like_spectrum(lib):
     w, v = eigh_tridiagonal(a, b, select="i", select_range=(0, 0))
     assert abs(th - w[0]) <= 1e-13 * abs(w[0])
     assert abs(abs(sl) - abs(v[-1, 0])) <= 1e-8
+
+
+def test_continued_fraction_matches_oracle(lib):
+    """hb_continued_fraction (host utility) against the oracle's evaluation of the same fraction."""
+    from oracle import response as R
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 40):
+        a = rng.normal(size=n) * 2
+        b = np.abs(rng.normal(size=n - 1)) + 0.1
+        z = np.linspace(-5, 5, 11) + 0.2j
+        got = pd.hb_continued_fraction(a, b, 0.7, -1.3, z)
+        want = R.continued_fraction(a, b, 0.7, -1.3, z)
+        assert np.max(np.abs(got - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
