@@ -334,6 +334,8 @@ def run_ours(args, world, rank, local):
     solve = None
     if not args.no_solve and rank == 0 and args.workload in ("hubbard4x4_half", "kspace4x4_K00"):
         solve = time_to_e0(pd, h, torch)
+    if not args.no_solve and rank == 0 and args.workload == "tilted18_half":
+        solve = precision_e0(pd, h, torch)
     del V
     h.close()
     if world > 1:
@@ -403,6 +405,26 @@ def time_to_e0(pd, h, torch):
         res[name] = {"seconds": round(dt, 4), "iterations": r.iterations, "iterations_f32": r.iterations_f32,
                      "E0": r.E0, "residual": r.residual, "converged": r.converged,
                      "abs_err_vs_oracle": (abs(r.E0 - gold) if gold is not None else None)}
+    return res
+
+
+def precision_e0(pd, h, torch):
+    """18-site tilted cluster: E0 with float32 vectors (float64 scalars) and with the float32 phase plus a
+    fixed-point finish, against the float64-grade fixed-point run of the same cluster and seed."""
+    res = {}
+    for name, kw in (("fx64", dict(dtype=torch.int64, tol=1e-10)),
+                     ("f32_only", dict(dtype=torch.float32, tol=1e-6)),
+                     ("mixed_f32_fx64finish", dict(dtype=torch.float32, fp64_finish="fx64", tol=1e-10))):
+        torch.cuda.empty_cache()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = pd.lanczos_ground_state(h, maxit=3000, seed=0, raise_on_error=False, **kw)
+        torch.cuda.synchronize()
+        res[name] = {"seconds": round(time.perf_counter() - t0, 3), "iterations": r.iterations,
+                     "iterations_f32": r.iterations_f32, "E0": r.E0, "residual": r.residual, "converged": r.converged}
+    ref = res["fx64"]["E0"]
+    for v in res.values():
+        v["abs_err_vs_fx64"] = abs(v["E0"] - ref)
     return res
 
 
