@@ -108,7 +108,9 @@ def hv_kernel_key(dtype: str, cfg: dict) -> str:
     if not cfg.get("split"):
         return base + ",true>"
     up = {"f64": "k_hv_up<{r},double>", "fx64": "k_hv_fx_up<{r},2>", "f32": "k_hv_up<{r},float>"}[dtype]
-    return (f"{base},true,row pass> + " + up.format(r=cfg.get("up_rows") or 1)
+    # the fixed-point row pass runs on the warp-blocked spin-down table
+    row = f"k_hv_fx_wb<{rows},2> (row pass)" if dtype == "fx64" else f"{base},false> (row pass)"
+    return (f"{row} + " + up.format(r=cfg.get("up_rows") or 1)
             + f" (block {cfg.get('up_block') or 256}, {cfg.get('up_threads') or 1024} threads)")
 
 
