@@ -109,7 +109,8 @@ def hv_kernel_key(dtype: str, cfg: dict) -> str:
         return base + ",true>"
     up = {"f64": "k_hv_up<{r},double>", "fx64": "k_hv_fx_up<{r},2>", "f32": "k_hv_up<{r},float>"}[dtype]
     # the fixed-point row pass runs on the warp-blocked spin-down table
-    row = f"k_hv_fx_wb<{rows},2> (row pass)" if dtype == "fx64" else f"{base},false> (row pass)"
+    row = {"fx64": f"k_hv_fx_wb<{rows},2> (row pass)", "f32": f"k_hv_f_wb<{rows}> (row pass)",
+           "f64": f"{base},false> (row pass)"}[dtype]
     return (f"{row} + " + up.format(r=cfg.get("up_rows") or 1)
             + f" (block {cfg.get('up_block') or 256}, {cfg.get('up_threads') or 1024} threads)")
 

@@ -138,7 +138,11 @@ hb_status paradeisos_unrank(hb_handle h, const uint64_t *idx, uint64_t *states, 
  * dt      HB_F64, HB_F32 or HB_FX64 (fixed point, see hubbard_fixed_point_bits):
  *         element type of x and y (length D each).
  * x, y    device vectors; must not overlap (HB_ERR_INVALID_ARG).
- * Every launch configuration (hb_hv_config) gives bit-identical results.
+ * Every launch configuration (hb_hv_config) gives bit-identical results for
+ * HB_F64 and HB_FX64.  For HB_F32 the one-kernel configurations agree bit for
+ * bit, and so do the split ones (hb_hv_config.split = 1).  The split float32
+ * row pass sums the spin-down hops per (amplitude class, sign) and then scales
+ * each sum by -t, so it agrees with the one-kernel form to float32 rounding.
  */
 hb_status hubbard_apply(hb_handle h, hb_dtype dt, const void *x, void *y, void *stream);
 

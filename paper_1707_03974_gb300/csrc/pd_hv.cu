@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "pd_hv_body.cuh"
+#include "pd_hv_f32wb.cuh"
 
 namespace {
 
@@ -122,12 +123,77 @@ hb_status launch_up(hb_handle h, const HvArgs<T> &a, const T *x, T *y, cudaStrea
                                    : launch_up_v<RR, T, IDX32, 1>(h, a, x, y, st, u);
 }
 
+template <int R, int NC, int LB>
+__global__ void __launch_bounds__(LB) k_hv_f_wb(const FWbArgs a, const float *__restrict__ x, float *__restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint64_t ngroups = (a.Du + R - 1) / R;
+    for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) hv_f_wb_group<R, NC>(a, x, y, g, smem);
+}
+
+template <int R, int NC>
+hb_status launch_f_wb(hb_handle h, const FWbArgs &a, const float *x, float *y, cudaStream_t st, int threads) {
+    auto kern = threads <= 512 ? k_hv_f_wb<R, NC, 512> : k_hv_f_wb<R, NC, 1024>;
+    const size_t smem = hv_f_wb_smem_bytes(R, a.Dd);
+    unsigned grid = 0;
+    hb_status s = persistent_launch_dims(h, kern, threads, smem, (a.Du + R - 1) / R, &grid);
+    if (s != HB_OK) return s;
+    kern<<<grid, threads, smem, st>>>(a, x, y);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+template <int R>
+hb_status launch_f_wb_r(hb_handle h, const FWbArgs &a, const float *x, float *y, cudaStream_t st, int threads) {
+    switch (std::max(1, h->n_classes)) {
+        case 1: return launch_f_wb<R, 1>(h, a, x, y, st, threads);
+        case 2: return launch_f_wb<R, 2>(h, a, x, y, st, threads);
+        case 3: return launch_f_wb<R, 3>(h, a, x, y, st, threads);
+        default: return launch_f_wb<R, 4>(h, a, x, y, st, threads);
+    }
+}
+
+// Float32 row pass of the split form on the warp-blocked spin-down table, when
+// the handle has one and R rows (requested, else the widest) fit in shared memory.
+hb_status f32_wb_row_pass(hb_handle h, const HvArgs<float> &a, const float *x, float *y, cudaStream_t st,
+                          const HvConfig &cfg, size_t budget, bool *done) {
+    *done = false;
+    if (!h->dn.wb_ok || h->dn.wb_nblk == 0) return HB_OK;
+    auto fits = [&](int R) { return hv_f_wb_smem_bytes(R, a.Dd) <= budget; };
+    int R = cfg.rows;
+    if (R != 1 && R != 2 && R != 4) R = 0;
+    if (R == 0 || !fits(R)) R = fits(4) ? 4 : fits(2) ? 2 : fits(1) ? 1 : 0;
+    if (R == 0) return HB_OK;
+    FWbArgs f;
+    f.Du = a.Du;
+    f.Dd = a.Dd;
+    f.U = a.U;
+    f.str_up = a.str_up;
+    f.order = a.order;
+    for (int c = 0; c < PD_FX_MAXC; ++c) f.tc[c] = c < h->n_classes ? (float)(-h->class_t[c]) : 0.0f;
+    f.wb_perm = h->dn.wb_perm;
+    f.wb_str = h->dn.wb_str;
+    f.wb_base = h->dn.wb_base;
+    f.wb_ent = h->dn.wb_ent;
+    f.wb_caps = h->dn.wb_caps;
+    f.wb_nblk = h->dn.wb_nblk;
+    const int threads = pick_threads(cfg, a.Dd);
+    *done = true;
+    if (R == 4) return launch_f_wb_r<4>(h, f, x, y, st, threads);
+    if (R == 2) return launch_f_wb_r<2>(h, f, x, y, st, threads);
+    return launch_f_wb_r<1>(h, f, x, y, st, threads);
+}
+
 template <typename T, bool DO_A>
 hb_status row_pass(hb_handle h, const HvArgs<T> &a, const T *x, T *y, cudaStream_t st, const HvConfig &cfg) {
     const int threads = pick_threads(cfg, a.Dd);
     int max_smem = 0;
     PD_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     const size_t budget = (size_t)max_smem;
+    if constexpr (std::is_same<T, float>::value && !DO_A) {
+        bool done = false;
+        hb_status s = f32_wb_row_pass(h, a, x, y, st, cfg, budget, &done);
+        if (s != HB_OK || done) return s;
+    }
     auto fits = [&](int R) { return hv_smem_bytes(R, a.zmax_up, sizeof(T), a.Dd, true) <= budget; };
     // requested row-group size if it fits, else the widest that fits
     int R = cfg.rows;

@@ -65,8 +65,14 @@ def test_hv_f32_matches_oracle(env, cl, nu, nd, U):
     x = x32.astype(np.float64)
     yr = apply(m, b, x)
     h = handle_for(cl, U, nu, nd)
+    bound = 64 * EPS32 * abs_bound(m, b, x) + 1e-30
     y = pd.hubbard_apply(h, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(y - yr) <= 64 * EPS32 * abs_bound(m, b, x) + 1e-30)
+    assert np.all(np.abs(y - yr) <= bound)
+    # split form (float32 row pass on the warp-blocked table, where the handle has one)
+    for rows in (1, 2, 4):
+        pd.hubbard_set_hv_config(h, torch.float32, rows, 256, 1, split=1)
+        y = pd.hubbard_apply(h, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(y - yr) <= bound), rows
     h.close()
 
 
