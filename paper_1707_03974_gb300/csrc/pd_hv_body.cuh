@@ -28,6 +28,33 @@ struct HvArgs {
     int zmax_up;
 };
 
+// Staging of R rows of x into shared memory, interleaved s_x[d * R + r]: every
+// element is an asynchronous global -> shared copy (cp.async, 4 or 8 bytes), so
+// a thread has all its copies in flight at once and waits once, instead of one
+// global-load round trip per element.  Rows r >= nr are filled with zeros.
+template <typename T, int R>
+__device__ __forceinline__ void stage_rows_async(T *s_x, const T *__restrict__ x, const uint64_t (&ur)[R], int nr,
+                                                 uint64_t Dd) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const T *xr = x + ur[r] * Dd;
+        for (uint64_t d = threadIdx.x; d < Dd; d += blockDim.x) {
+            T *dst = s_x + d * R + r;
+            if (r < nr) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+                if constexpr (sizeof(T) == 8)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(xr + d) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(xr + d) : "memory");
+            } else {
+                *dst = T(0);
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Shared memory of a float group: [up row offsets R*zmax u64][up vals R*zmax T][up counts R int][x rows R*Dd T]
 __host__ __device__ inline size_t hv_smem_bytes(int R, int zmax, size_t tsize, uint64_t Dd, bool smem_rows) {
     const int zr = zmax > 0 ? zmax : 1;
@@ -73,14 +100,7 @@ __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict
             }
         }
     }
-    if (SMEM) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (r >= nr) break;
-            const T *xr = x + ur[r] * Dd;
-            for (uint64_t d = threadIdx.x; d < Dd; d += blockDim.x) s_x[d * R + r] = xr[d];
-        }
-    }
+    if (SMEM) stage_rows_async<T, R>(s_x, x, ur, nr, Dd);
     __syncthreads();
     uint32_t su[R];
 #pragma unroll
@@ -218,14 +238,7 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
             }
         }
     }
-    if (SMEM) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (r >= nr) break;
-            const int64_t *xr = x + ur[r] * Dd;
-            for (uint64_t d = threadIdx.x; d < Dd; d += blockDim.x) s_x[d * R + r] = xr[d];
-        }
-    }
+    if (SMEM) stage_rows_async<int64_t, R>(s_x, x, ur, nr, Dd);
     __syncthreads();
     uint32_t su[R];
 #pragma unroll
@@ -559,11 +572,7 @@ __device__ __forceinline__ void hv_fx_wb_group(const FxArgs &a, const int64_t *_
 #pragma unroll
     for (int r = 0; r < R; ++r) ur[r] = r < nr ? (a.order ? (uint64_t)a.order[p0 + r] : p0 + r) : 0;
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int64_t *xr = x + ur[r] * Dd;
-        for (uint64_t d = threadIdx.x; d < Dd; d += blockDim.x) s_x[d * R + r] = r < nr ? xr[d] : 0;
-    }
+    stage_rows_async<int64_t, R>(s_x, x, ur, nr, Dd);
     if (threadIdx.x < 8 * R) s_x[Dd * R + threadIdx.x] = 0;
     __syncthreads();
     uint32_t su[R];

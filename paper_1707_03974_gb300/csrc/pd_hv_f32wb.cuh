@@ -50,62 +50,87 @@ __device__ __forceinline__ void hv_f_wb_group(const FWbArgs &a, const float *__r
 #pragma unroll
     for (int r = 0; r < R; ++r) ur[r] = r < nr ? (a.order ? (uint64_t)a.order[p0 + r] : p0 + r) : 0;
     __syncthreads();  // the previous group is done with shared memory
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float *xr = x + ur[r] * Dd;
-        for (uint64_t d = threadIdx.x; d < Dd; d += blockDim.x) s_x[d * R + r] = r < nr ? xr[d] : 0.0f;
-    }
+    stage_rows_async<float, R>(s_x, x, ur, nr, Dd);
     if (threadIdx.x < 8 * R) s_x[Dd * R + threadIdx.x] = 0.0f;
     __syncthreads();
     uint32_t su[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) su[r] = r < nr ? a.str_up[ur[r]] : 0u;
     const int lane = threadIdx.x & 31;
-    for (uint32_t b = threadIdx.x >> 5; b < a.wb_nblk; b += blockDim.x >> 5) {
-        const uint64_t caps = a.wb_caps[b];
-        const uint32_t *ent = a.wb_ent + (uint64_t)a.wb_base[b] * 32 + lane;
-        float acc[R][2 * NC];
+    // With one staged row (one CTA per SM) a warp runs two warp blocks side by side,
+    // so that twice as many table loads are in flight; the block with fewer slot
+    // pairs in a segment reads the zero element s_x[D_dn] (adding +0).
+    constexpr int PB = R == 1 ? 2 : 1;
+    const uint32_t nw = blockDim.x >> 5;
+    const uint32_t zpair = (uint32_t)Dd | ((uint32_t)Dd << 16);
+    for (uint32_t b0 = (threadIdx.x >> 5) * PB; b0 < a.wb_nblk; b0 += nw * PB) {
+        uint64_t caps[PB];
+        const uint32_t *ent[PB];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+        for (int j = 0; j < PB; ++j) {
+            const bool ok = b0 + j < a.wb_nblk;
+            caps[j] = ok ? a.wb_caps[b0 + j] : 0ull;
+            ent[j] = a.wb_ent + (ok ? (uint64_t)a.wb_base[b0 + j] * 32 : 0ull) + lane;
+        }
+        float acc[PB][R][2 * NC];
 #pragma unroll
-            for (int q = 0; q < 2 * NC; ++q) acc[r][q] = 0.0f;
+        for (int j = 0; j < PB; ++j)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int q = 0; q < 2 * NC; ++q) acc[j][r][q] = 0.0f;
 #pragma unroll
         for (int q = 0; q < 2 * NC; ++q) {
-            const int np = (int)((caps >> (8 * q)) & 0xFFu);
+            int np[PB], npm = 0;
+#pragma unroll
+            for (int j = 0; j < PB; ++j) {
+                np[j] = (int)((caps[j] >> (8 * q)) & 0xFFu);
+                npm = np[j] > npm ? np[j] : npm;
+            }
             int s = 0;
-            for (; s + 4 <= np; s += 4) {
-                uint32_t e[4];
+            for (; s + 4 <= npm; s += 4) {
+                uint32_t e[PB][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) e[i] = ent[(s + i) * 32];
+                for (int j = 0; j < PB; ++j)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < 4; ++i) e[j][i] = s + i < np[j] ? ent[j][(s + i) * 32] : zpair;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < PB; ++j) {
+                        float v0[R], v1[R];
+                        f_wb_load<R>(s_x, e[j][i] & 0xFFFFu, v0);
+                        f_wb_load<R>(s_x, e[j][i] >> 16, v1);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) acc[j][r][q] += v0[r] + v1[r];
+                    }
+            }
+            for (; s < npm; ++s)
+#pragma unroll
+                for (int j = 0; j < PB; ++j) {
+                    const uint32_t ev = s < np[j] ? ent[j][s * 32] : zpair;
                     float v0[R], v1[R];
-                    f_wb_load<R>(s_x, e[i] & 0xFFFFu, v0);
-                    f_wb_load<R>(s_x, e[i] >> 16, v1);
+                    f_wb_load<R>(s_x, ev & 0xFFFFu, v0);
+                    f_wb_load<R>(s_x, ev >> 16, v1);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r][q] += v0[r] + v1[r];
+                    for (int r = 0; r < R; ++r) acc[j][r][q] += v0[r] + v1[r];
                 }
-            }
-            for (; s < np; ++s) {
-                const uint32_t ev = ent[s * 32];
-                float v0[R], v1[R];
-                f_wb_load<R>(s_x, ev & 0xFFFFu, v0);
-                f_wb_load<R>(s_x, ev >> 16, v1);
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r][q] += v0[r] + v1[r];
-            }
-            ent += np * 32;
+            for (int j = 0; j < PB; ++j) ent[j] += np[j] * 32;
         }
-        const uint32_t p = b * 32 + lane;
-        const uint32_t col = a.wb_perm[p];
-        if (col < Dd) {
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+            if (b0 + j >= a.wb_nblk) break;
+            const uint32_t p = (b0 + j) * 32 + lane;
+            const uint32_t col = a.wb_perm[p];
+            if (col >= Dd) continue;
             const uint32_t sd = a.wb_str[p];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (r >= nr) continue;
                 float out = a.U * (float)__popc(su[r] & sd) * s_x[(uint64_t)col * R + r];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) out += a.tc[c] * (acc[r][2 * c] - acc[r][2 * c + 1]);
+                for (int c = 0; c < NC; ++c) out += a.tc[c] * (acc[j][r][2 * c] - acc[j][r][2 * c + 1]);
                 y[ur[r] * Dd + col] = out;
             }
         }
