@@ -258,47 +258,55 @@ void free_spin(SpinTables &s) {
     s = SpinTables();
 }
 
-// Shared-memory bank groups: the row pass reads 16-byte elements (two staged
-// rows), served 8 lanes (one quarter warp) at a time over 8 groups of 4 banks;
-// targets t and t' of one quarter warp in one slot conflict when t = t' mod 8
-// and t != t', and a slot costs as many shared-memory wavefronts as its most
-// used group.  The sums are exact integer sums, so the order of a lane's hops
-// within a segment is free.  Per quarter warp, the slots are filled in order:
-// each slot takes a maximum matching of lanes to distinct groups (augmenting
-// paths; lanes whose remaining hops fill every remaining slot first, groups
-// with the most remaining hops preferred), and a lane that must place a hop
-// but found no free group joins its least used group.  A local search then
-// swaps two slots of one lane when that lowers the summed worst-group load of
-// the two slots.  On the 4x4 half-filled table this gives ~5.8 wavefronts per
-// 16-byte gather in the model above (the search alone: ~7.5; a lower bound for
-// any order within segments: 5.5).
-void match_slots(std::vector<int32_t> &grid, int slots, int qw) {
+// Shared-memory bank groups.  A slot of the row pass is one shared load per
+// lane, and costs as many wavefronts as the most used bank group among the
+// lanes served together (distinct targets in one group conflict).  Two layouts:
+//  * 16-byte elements (two staged fixed-point rows, or four float32 rows):
+//    8 lanes (one quarter warp) at a time over 8 groups of 4 banks, group t % 8;
+//  * 4-byte elements (one staged float32 row, for rows too long to stage two
+//    fixed-point rows): all 32 lanes over the 32 banks, bank t % 32.
+// The sums are exact integer sums (and float32 sums in a fixed order), so the
+// order of a lane's hops within a segment is free.  Per lane set, the slots are
+// filled in order: each slot takes a maximum matching of lanes to distinct
+// groups (augmenting paths; lanes whose remaining hops fill every remaining
+// slot first, groups with the most remaining hops preferred), and a lane that
+// must place a hop but found no free group joins its least used group.  A local
+// search then swaps two slots of one lane when that lowers the summed
+// worst-group load of the two slots.  On the 4x4 half-filled table the 16-byte
+// layout measures 5.3 wavefronts per gather (natural order 8.9, the local
+// search alone 7.0).
+struct BankLayout {
+    int NL;  // lanes served together
+    int G;   // bank groups
+};
+
+void match_slots(std::vector<int32_t> &grid, int slots, int l0, const BankLayout &bl) {
+    const int NL = bl.NL, G = bl.G;
     auto at = [&](int l, int s) -> int32_t & { return grid[(size_t)l * slots + s]; };
-    std::vector<int32_t> rem[8];
-    for (int i = 0; i < 8; ++i)
+    std::vector<std::vector<int32_t>> rem(NL);
+    for (int i = 0; i < NL; ++i)
         for (int s = 0; s < slots; ++s)
-            if (at(8 * qw + i, s) >= 0) rem[i].push_back(at(8 * qw + i, s));
+            if (at(l0 + i, s) >= 0) rem[i].push_back(at(l0 + i, s));
+    std::vector<int> dem(G), lanes(NL), gown(G), choice(NL), mult(G);
     for (int s = 0; s < slots; ++s) {
         const int R = slots - s;
-        int dem[8] = {0};
-        for (int i = 0; i < 8; ++i)
-            for (int32_t t : rem[i]) ++dem[t % 8];
-        int lanes[8];
-        for (int i = 0; i < 8; ++i) lanes[i] = i;
-        std::stable_sort(lanes, lanes + 8, [&](int a, int b) {
+        std::fill(dem.begin(), dem.end(), 0);
+        for (int i = 0; i < NL; ++i)
+            for (int32_t t : rem[i]) ++dem[t % G];
+        for (int i = 0; i < NL; ++i) lanes[i] = i;
+        std::stable_sort(lanes.begin(), lanes.end(), [&](int a, int b) {
             const bool ma = (int)rem[a].size() >= R, mb = (int)rem[b].size() >= R;
             if (ma != mb) return ma;
             return rem[a].size() > rem[b].size();
         });
-        int gown[8], choice[8];
-        for (int g = 0; g < 8; ++g) gown[g] = -1;
-        for (int i = 0; i < 8; ++i) choice[i] = -1;
-        // augmenting path from lane i over groups not yet visited (mask)
-        std::function<bool(int, unsigned &)> augment = [&](int i, unsigned &seen) -> bool {
-            int opts[8], no = 0;
-            unsigned have = 0;
-            for (int32_t t : rem[i]) have |= 1u << (t % 8);
-            for (int g = 0; g < 8; ++g)
+        std::fill(gown.begin(), gown.end(), -1);
+        std::fill(choice.begin(), choice.end(), -1);
+        // augmenting path from lane i over groups not yet visited (seen)
+        std::function<bool(int, uint32_t &)> augment = [&](int i, uint32_t &seen) -> bool {
+            uint32_t have = 0;
+            for (int32_t t : rem[i]) have |= 1u << (t % G);
+            int opts[32], no = 0;
+            for (int g = 0; g < G; ++g)
                 if (have >> g & 1u) opts[no++] = g;
             std::stable_sort(opts, opts + no, [&](int a, int b) { return dem[a] > dem[b]; });
             for (int k = 0; k < no; ++k) {
@@ -313,30 +321,30 @@ void match_slots(std::vector<int32_t> &grid, int slots, int qw) {
             }
             return false;
         };
-        for (int k = 0; k < 8; ++k) {
-            unsigned seen = 0;
+        for (int k = 0; k < NL; ++k) {
+            uint32_t seen = 0;
             if (!rem[lanes[k]].empty()) augment(lanes[k], seen);
         }
-        int mult[8] = {0};
-        for (int i = 0; i < 8; ++i)
+        std::fill(mult.begin(), mult.end(), 0);
+        for (int i = 0; i < NL; ++i)
             if (choice[i] >= 0) ++mult[choice[i]];
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < NL; ++k) {
             const int i = lanes[k];
             if (choice[i] >= 0 || (int)rem[i].size() < R) continue;
             int best = -1;
             for (int32_t t : rem[i]) {
-                const int g = t % 8;
+                const int g = t % G;
                 if (best < 0 || mult[g] < mult[best] || (mult[g] == mult[best] && dem[g] > dem[best])) best = g;
             }
             choice[i] = best;
             ++mult[best];
         }
-        for (int i = 0; i < 8; ++i) {
-            at(8 * qw + i, s) = -1;
+        for (int i = 0; i < NL; ++i) {
+            at(l0 + i, s) = -1;
             if (choice[i] < 0) continue;
             for (size_t k = 0; k < rem[i].size(); ++k)
-                if (rem[i][k] % 8 == choice[i]) {
-                    at(8 * qw + i, s) = rem[i][k];
+                if (rem[i][k] % G == choice[i]) {
+                    at(l0 + i, s) = rem[i][k];
                     rem[i].erase(rem[i].begin() + (long)k);
                     break;
                 }
@@ -344,36 +352,37 @@ void match_slots(std::vector<int32_t> &grid, int slots, int qw) {
     }
 }
 
-void balance_banks(std::vector<int32_t> &grid, int slots) {
+void balance_banks(std::vector<int32_t> &grid, int slots, const BankLayout &bl) {
     if (slots < 2) return;
-    for (int qw = 0; qw < 4; ++qw) {
-        match_slots(grid, slots, qw);
-        std::vector<int> cnt((size_t)slots * 8, 0);
+    const int NL = bl.NL, G = bl.G;
+    for (int l0 = 0; l0 < 32; l0 += NL) {
+        match_slots(grid, slots, l0, bl);
+        std::vector<int> cnt((size_t)slots * G, 0);
         auto at = [&](int l, int s) -> int32_t & { return grid[(size_t)l * slots + s]; };
-        for (int l = 8 * qw; l < 8 * qw + 8; ++l)
+        for (int l = l0; l < l0 + NL; ++l)
             for (int s = 0; s < slots; ++s)
-                if (at(l, s) >= 0) ++cnt[(size_t)s * 8 + at(l, s) % 8];
+                if (at(l, s) >= 0) ++cnt[(size_t)s * G + at(l, s) % G];
         auto worst = [&](int s) {
             int m = 0;
-            for (int g = 0; g < 8; ++g) m = std::max(m, cnt[(size_t)s * 8 + g]);
+            for (int g = 0; g < G; ++g) m = std::max(m, cnt[(size_t)s * G + g]);
             return m;
         };
         for (int pass = 0; pass < 4; ++pass) {
             bool improved = false;
-            for (int l = 8 * qw; l < 8 * qw + 8; ++l)
+            for (int l = l0; l < l0 + NL; ++l)
                 for (int s1 = 0; s1 < slots; ++s1)
                     for (int s2 = s1 + 1; s2 < slots; ++s2) {
                         const int32_t a = at(l, s1), b = at(l, s2);
                         if (a == b) continue;
                         const int before = worst(s1) + worst(s2);
-                        if (a >= 0) --cnt[(size_t)s1 * 8 + a % 8], ++cnt[(size_t)s2 * 8 + a % 8];
-                        if (b >= 0) --cnt[(size_t)s2 * 8 + b % 8], ++cnt[(size_t)s1 * 8 + b % 8];
+                        if (a >= 0) --cnt[(size_t)s1 * G + a % G], ++cnt[(size_t)s2 * G + a % G];
+                        if (b >= 0) --cnt[(size_t)s2 * G + b % G], ++cnt[(size_t)s1 * G + b % G];
                         if (worst(s1) + worst(s2) < before) {
                             std::swap(at(l, s1), at(l, s2));
                             improved = true;
                         } else {
-                            if (a >= 0) ++cnt[(size_t)s1 * 8 + a % 8], --cnt[(size_t)s2 * 8 + a % 8];
-                            if (b >= 0) ++cnt[(size_t)s2 * 8 + b % 8], --cnt[(size_t)s1 * 8 + b % 8];
+                            if (a >= 0) ++cnt[(size_t)s1 * G + a % G], --cnt[(size_t)s2 * G + a % G];
+                            if (b >= 0) ++cnt[(size_t)s2 * G + b % G], --cnt[(size_t)s1 * G + b % G];
                         }
                     }
             if (!improved) break;
@@ -383,7 +392,7 @@ void balance_banks(std::vector<int32_t> &grid, int slots) {
 
 // Warp-blocked hop table (see SpinTables): built on the host from the
 // segment-ordered fixed-point hop lists.
-hb_status build_wb(SpinTables &st) {
+hb_status build_wb(SpinTables &st, int device) {
     const uint64_t D = st.D;
     if (D == 0 || D + 8 > 65535 || !st.ftarget) return HB_OK;
     const uint32_t kZeroSlot = 0xFFFFu;  // placeholder until the bank group is chosen
@@ -395,6 +404,13 @@ hb_status build_wb(SpinTables &st) {
     PD_CUDA(cudaMemcpy(str.data(), st.str, D * 4, cudaMemcpyDeviceToHost));
     constexpr int NQ = 2 * PD_FX_MAXC;
     auto cnt = [&](uint64_t r, int q) { return (int)((seg[r] >> (8 * q)) & 0xFFu); };
+    // bank layout of the row pass that will read this table: two staged 8-byte
+    // rows (16-byte gathers) when they fit in the largest shared-memory carve-out,
+    // else one staged float32 row (4-byte gathers)
+    int max_smem = 0;
+    PD_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    const bool wide = (uint64_t)2 * (D + 8) * 8 + 1024 <= (uint64_t)max_smem;
+    const BankLayout bl = wide ? BankLayout{8, 8} : BankLayout{32, 32};
     std::vector<uint32_t> perm(D);
     for (uint64_t r = 0; r < D; ++r) perm[r] = (uint32_t)r;
     std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) {
@@ -430,7 +446,7 @@ hb_status build_wb(SpinTables &st) {
                 for (int qq = 0; qq < q; ++qq) k0 += cnt(r, qq);
                 for (int i = 0; i < cnt(r, q); ++i) grid[(size_t)l * slots + i] = (int32_t)ft[(uint64_t)(k0 + i) * D + r];
             }
-            balance_banks(grid, slots);
+            balance_banks(grid, slots, bl);
             for (int s = 0; s < pairs; ++s, ++rows)
                 for (int l = 0; l < 32; ++l) {
                     uint32_t t[2];
@@ -442,22 +458,22 @@ hb_status build_wb(SpinTables &st) {
                 }
         }
     }
-    // empty slots read one of the eight zero elements s_x[D .. D+7]: the one in
-    // the bank group that no real target of the lane's quarter warp uses
+    // empty slots read one of the eight zero elements s_x[D .. D+7]: one in a
+    // bank group that no real target of the lanes served with it uses
     for (uint64_t b = 0, row = 0; b < nblk; ++b)
         for (int q = 0; q < NQ; ++q)
             for (uint64_t pr = 0; pr < ((caps[b] >> (8 * q)) & 0xFFu); ++pr, ++row)
                 for (int h = 0; h < 2; ++h)
-                    for (int qw = 0; qw < 4; ++qw) {
-                        bool used[8] = {false};
-                        for (int l = 8 * qw; l < 8 * qw + 8; ++l) {
+                    for (int l0 = 0; l0 < 32; l0 += bl.NL) {
+                        bool used[32] = {false};
+                        for (int l = l0; l < l0 + bl.NL; ++l) {
                             const uint32_t t = (ent[row * 32 + l] >> (16 * h)) & 0xFFFFu;
-                            if (t != kZeroSlot) used[t % 8] = true;
+                            if (t != kZeroSlot) used[t % bl.G] = true;
                         }
                         int z = 0;
-                        while (z < 7 && used[z]) ++z;
-                        const uint32_t zt = (uint32_t)D + (uint32_t)((z - (int)(D % 8) + 8) % 8);
-                        for (int l = 8 * qw; l < 8 * qw + 8; ++l) {
+                        while (z < 7 && used[(D + z) % bl.G]) ++z;
+                        const uint32_t zt = (uint32_t)D + (uint32_t)z;
+                        for (int l = l0; l < l0 + bl.NL; ++l) {
                             uint32_t &e = ent[row * 32 + l];
                             if (((e >> (16 * h)) & 0xFFFFu) == kZeroSlot)
                                 e = (e & ~(0xFFFFu << (16 * h))) | (zt << (16 * h));
@@ -511,7 +527,7 @@ hb_status build_spin(hb_handle h, SpinTables &st, int n) {
         PD_CUDA(cudaGetLastError());
     }
     PD_CUDA(cudaDeviceSynchronize());
-    if (h->fx_ok) return build_wb(st);
+    if (h->fx_ok) return build_wb(st, h->device);
     return HB_OK;
 }
 
