@@ -375,6 +375,8 @@ def run_ours(args, world, rank, local):
     bps = HV_BYTES_PER_STATE if args.dtype != "f32" else 8
     achieved = bps * D / (hv_ms * 1e-3) / 1e9
     kname = hv_kernel_key(args.dtype, tuned)
+    if "K" in wk:  # momentum sector: one row-factorised kernel
+        kname = {"fx64": "k_k_hv_rows<int64>", "f64": "k_k_hv_rows<double>", "f32": "k_k_hv_rows<float>"}[args.dtype]
     traffic = ncu_traffic(kname)
     out = {
         "metric": METRIC, "value": round(job_throughput(D, world, ms), 4), "unit": UNIT, "n_gpus": world,
