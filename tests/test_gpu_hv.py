@@ -219,3 +219,42 @@ def test_fx64_rejected_for_too_many_amplitudes(env):
     # the float paths still work
     pd.hubbard_apply(h, torch.zeros(h.D, dtype=torch.float64, device="cuda"))
     h.close()
+
+
+def _many_amplitudes(L, classes):
+    """Ring of L sites plus next-nearest bonds, amplitudes cycling through `classes` values."""
+    pairs = [(i, (i + 1) % L) for i in range(L)] + [(i, (i + 2) % L) for i in range(0, L, 2)]
+    t = tuple(classes[k % len(classes)] for k in range(len(pairs)))
+    return wl.Cluster(f"ring{L}_{len(classes)}amp", L, tuple(pairs), t)
+
+
+@pytest.mark.parametrize("L,classes,nu,nd,U", [(9, (1.0, 0.6, -0.25), 4, 3, 3.0),
+                                               (10, (1.0, 0.7, -0.3, 0.45), 5, 4, 6.0)])
+def test_hv_split_many_amplitudes(env, L, classes, nu, nd, U):
+    """Split H·v with 3 and 4 amplitude classes (6 and 8 segments per warp block of the
+    warp-blocked table), fixed point and float32, every row-group size, against the oracle."""
+    torch, pd = env
+    cl = _many_amplitudes(L, classes)
+    m = Model.from_cluster(cl, U, nu, nd)
+    b = Basis(cl.L, nu, nd)
+    h = handle_for(cl, U, nu, nd)
+    F = pd.hubbard_fixed_point_bits(h)
+    x = start_vector(21, b.D)
+    q = pd.hubbard_convert(h, torch.from_numpy(x).cuda(), torch.int64)
+    xq = np.ldexp(q.cpu().numpy().astype(np.float64), -F)
+    yr = apply(m, b, xq)
+    bound = (len(classes) + 2) * 2.0 ** -F + 64 * EPS64 * abs_bound(m, b, xq)
+    for rows in (1, 2):
+        for order in (0, 1):
+            pd.hubbard_set_hv_config(h, torch.int64, rows, 256, order, split=1, up_block=64, up_threads=256, up_rows=2)
+            y = pd.hubbard_convert(h, pd.hubbard_apply(h, q), torch.float64).cpu().numpy()
+            assert np.all(np.abs(y - yr) <= bound), (rows, order)
+    x32 = x.astype(np.float32)
+    yr32 = apply(m, b, x32.astype(np.float64))
+    bound32 = 64 * EPS32 * abs_bound(m, b, x32.astype(np.float64)) + 1e-30
+    for rows in (1, 2, 4):
+        pd.hubbard_set_hv_config(h, torch.float32, rows, 512, 1, split=1)
+        y = pd.hubbard_apply(h, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(y - yr32) <= bound32), rows
+    assert pd.hubbard_last_error(h) == "HB_OK"
+    h.close()
