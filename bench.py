@@ -392,6 +392,8 @@ def run_ours(args, world, rank, local):
         "hv_config": tuned,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
+                     # DRAM bytes the kernels actually move (committed ncu capture) over the same time
+                     "dram_gbs": round(traffic / (hv_ms * 1e-3) / 1e9, 1) if traffic else None,
                      "kernel": kname, "bytes_per_state": bps,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "e2e": {"value": round(job_throughput(D, world, e2e_ms), 4), "unit": UNIT,
