@@ -440,9 +440,17 @@ def time_to_e0(pd, h, torch):
 
 def precision_e0(pd, h, torch):
     """18-site tilted cluster: E0 with float32 vectors (float64 scalars) and with the float32 phase plus a
-    fixed-point finish, against the float64-grade fixed-point run of the same cluster and seed."""
+    fixed-point finish, against the float64-grade fixed-point run of the same cluster and seed, and the
+    plain float64 solve for time.  Each vector type's H·v launch configuration is autotuned first."""
+    for dt in (torch.int64, torch.float64):
+        xa = torch.zeros(h.D, dtype=dt, device="cuda")
+        ya = torch.empty_like(xa)
+        pd.hubbard_autotune(h, xa, ya, reps=1)
+        del xa, ya
+        torch.cuda.empty_cache()
     res = {}
     for name, kw in (("fx64", dict(dtype=torch.int64, tol=1e-10)),
+                     ("plain_f64", dict(dtype=torch.float64, tol=1e-10)),
                      ("f32_only", dict(dtype=torch.float32, tol=1e-6)),
                      ("mixed_f32_fx64finish", dict(dtype=torch.float32, fp64_finish="fx64", tol=1e-10))):
         torch.cuda.empty_cache()
