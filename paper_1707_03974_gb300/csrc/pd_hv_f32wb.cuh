@@ -57,10 +57,10 @@ __device__ __forceinline__ void hv_f_wb_group(const FWbArgs &a, const float *__r
 #pragma unroll
     for (int r = 0; r < R; ++r) su[r] = r < nr ? a.str_up[ur[r]] : 0u;
     const int lane = threadIdx.x & 31;
-    // With one staged row (one CTA per SM) a warp runs two warp blocks side by side,
-    // so that twice as many table loads are in flight; the block with fewer slot
+    // With one staged row (one CTA per SM) a warp runs four warp blocks side by side,
+    // so that four times as many table loads are in flight; a block with fewer slot
     // pairs in a segment reads the zero element s_x[D_dn] (adding +0).
-    constexpr int PB = R == 1 ? 2 : 1;
+    constexpr int PB = R == 1 ? 4 : 1;
     const uint32_t nw = blockDim.x >> 5;
     const uint32_t zpair = (uint32_t)Dd | ((uint32_t)Dd << 16);
     for (uint32_t b0 = (threadIdx.x >> 5) * PB; b0 < a.wb_nblk; b0 += nw * PB) {
