@@ -34,7 +34,7 @@ def _stale(lib: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "pd_common.cuh"), os.path.join(CSRC, "pd_hv_body.cuh"), os.path.join(CSRC, "pd_hv_f32wb.cuh"), os.path.join(CSRC, "pd_tc.cuh"), os.path.join(ROOT, "include", "paradeisos_mlp.h"),
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "pd_common.cuh"), os.path.join(CSRC, "pd_hv_body.cuh"), os.path.join(CSRC, "pd_hv_f32wb.cuh"), os.path.join(CSRC, "pd_wb_sched.h"), os.path.join(CSRC, "pd_tc.cuh"), os.path.join(ROOT, "include", "paradeisos_mlp.h"),
                                                        os.path.join(ROOT, "include", "paradeisos.h")]
     if not force and not _stale(LIB, deps):
         return LIB
