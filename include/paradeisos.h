@@ -155,7 +155,10 @@ typedef struct {
     float ms;                 /* hubbard_autotune: time per H·v of the chosen configuration */
     int32_t split;            /* 0: one kernel for all terms; 1: a row pass (diagonal + spin-down hops, the
                                  fields above) then a spin-up pass over column blocks of x, so the blocks
-                                 in flight stay in L2 (the fields below) */
+                                 in flight stay in L2 (the fields below).  For HB_FX64 and HB_F32 the row
+                                 pass reads the handle's warp-blocked spin-down table when it has one (at
+                                 most 4 distinct hopping amplitudes, at most 255 bonds, D_dn + 8 <= 65535):
+                                 HB_FX64 stages 1 or 2 rows, HB_F32 1, 2 or 4 */
     int32_t up_block;         /* split: columns per block, multiple of 32, <= up_threads (0 = 256) */
     int32_t up_threads;       /* split: threads per CTA, a multiple of up_block, <= 1024 (0 = 1024) */
     int32_t up_rows;          /* split: rows per thread, 1, 2 or 4 (0 = 1) */
