@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="hubbard4x4_half",
-                   choices=sorted(WORKLOADS) + ["batch64", "learned4x4", "start4x4", "green4x4"])
+                   choices=sorted(WORKLOADS) + ["batch64", "learned4x4", "start4x4", "green4x4", "ceilings"])
     p.add_argument("--dtype", default="fx64", choices=["f64", "fx64", "f32"],
                    help="Krylov vector type: fixed-point int64 (default, float64-grade accuracy without the "
                         "float64 pipe), float64 (float64 FMAs), float32")
@@ -277,26 +277,34 @@ def run_ours(args, world, rank, local):
     ab = beta[:nsteps].cpu().numpy()
     sane = bool((ab > 0).all())
 
+    # the two passes of the H·v timed separately (events between them), for the on-chip rooflines
+    pass_ms = hv_pass_times(pd, h, V[nsteps % 3], V[(nsteps + 1) % 3], torch)
+    ceil = measure_ceilings(pd, torch, dev)
+
     # end to end through the public API with host buffers: every step copies its input vector
-    # from pinned host memory and reads alpha, beta back to the host.  The copies run on a
-    # second stream into one of two device buffers, so the copy for step j + 1 overlaps the
-    # compute of step j; step j waits for its own copy, and a buffer is refilled only after
-    # the step that read it
+    # from pinned host memory and reads alpha, beta back to the host; w stays on the device.
+    # Each step is the general three-term step (with vprev and beta_prev, like the timed
+    # region).  The copies run on a second stream into a ring of three device buffers, so the
+    # copy for step j + 1 overlaps the compute of step j; step j waits for its own copy, and
+    # a buffer is refilled only after the last step that read it (as v, then as vprev)
     host_v = torch.empty(D, dtype=vdt, pin_memory=True)
     host_v.copy_(V[nsteps % 3])
     host_ab = torch.empty(2, dtype=torch.float64, pin_memory=True)
     e2e_steps = max(3, min(args.steps, 10))
     copy_stream = torch.cuda.Stream(device=dev)
-    bufs = (V[0], V[2])
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    used = [torch.cuda.Event(), torch.cuda.Event()]
+    ring = (V[0], V[2], torch.empty(D, dtype=vdt, device=dev))
+    w_out = V[1]
+    ring[2].copy_(V[0])
+    bprev_e2e = beta[nsteps - 1:nsteps]
+    copied = [torch.cuda.Event() for _ in range(3)]
+    used = [torch.cuda.Event() for _ in range(3)]
 
     def issue_copy(j):
-        b = j % 2
-        if j >= 2:
+        b = j % 3
+        if j >= 2:  # ring[b] was last read (as vprev) by step j - 2
             copy_stream.wait_event(used[b])
         with torch.cuda.stream(copy_stream):
-            bufs[b].copy_(host_v, non_blocking=True)
+            ring[b].copy_(host_v, non_blocking=True)
         copied[b].record(copy_stream)
 
     torch.cuda.synchronize()
@@ -307,10 +315,10 @@ def run_ours(args, world, rank, local):
     for j in range(e2e_steps):
         if j + 1 < e2e_steps:
             issue_copy(j + 1)
-        b = j % 2
+        b, bp = j % 3, (j - 1) % 3
         stream.wait_event(copied[b])
-        pd.lanczos_step(h, bufs[b], None, V[1], None, alpha[0:1], beta[0:1], scratch)
-        used[b].record(stream)
+        pd.lanczos_step(h, ring[b], ring[bp], w_out, bprev_e2e, alpha[0:1], beta[0:1], scratch)
+        used[bp].record(stream)  # ring[bp] has been read for the last time (as vprev)
         host_ab[0:1].copy_(alpha[0:1], non_blocking=True)
         host_ab[1:2].copy_(beta[0:1], non_blocking=True)
     t1e.record(stream)
@@ -318,6 +326,7 @@ def run_ours(args, world, rank, local):
     e2e_ms = t0e.elapsed_time(t1e) / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     host_bytes = host_v.element_size()
+    del ring, w_out
 
     # the same step with plain float64 vectors and float64 FMAs, for comparison
     plain = None
@@ -398,11 +407,16 @@ def run_ours(args, world, rank, local):
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "e2e": {"value": round(job_throughput(D, world, e2e_ms), 4), "unit": UNIT,
                 "h2d_bytes_per_step": D * host_bytes, "d2h_bytes_per_step": 16,
+                "step": "the general three-term step (v from the host, vprev and beta_prev resident), as timed above",
+                "output": "alpha and beta are read back each step; w stays on the device",
                 "overlap": "each step's input copy runs on a second stream while the previous step computes"},
         "gpu_launches": int(launches.value),
         "clocks": clk,
         "recurrence_sane": sane,
     }
+    if "K" not in wk:
+        out["roofline"]["onchip"] = onchip_roofline(cl, wk, args.dtype, tuned, pass_ms, ceil, D, peak)
+    out["ceilings"] = ceil
     if plain:
         out["plain_f64_step"] = plain
     if solve:
@@ -412,6 +426,73 @@ def run_ours(args, world, rank, local):
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+    return out
+
+
+def hv_pass_times(pd, h, x, y, torch, reps=10):
+    """Mean ms of the H·v's row pass and spin-up pass over reps applications (events between them)."""
+    evs = []
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        pd.hubbard_apply_timed(h, x, y, *e)
+        evs.append(e)
+    torch.cuda.synchronize()
+    row = statistics.mean(a.elapsed_time(b) for a, b, _ in evs)
+    up = statistics.mean(b.elapsed_time(c) for _, b, c in evs)
+    return {"row_pass_ms": round(row, 4), "up_pass_ms": round(up, 4)}
+
+
+def measure_ceilings(pd, torch, dev):
+    """On-chip rates of this GPU, measured by the library's probe kernels (hb_measure_ceilings)."""
+    buf = torch.empty(1 << 31, dtype=torch.uint8, device=dev)
+    c = pd.hb_measure_ceilings(buf)
+    del buf
+    torch.cuda.empty_cache()
+    keep = ("sm_clock_mhz", "fp64_fma_tflops", "fp32_fma_tflops", "int32_add_tops", "int64_add_tops",
+            "smem_seq16_gbs", "smem_gather8_gbs", "smem_gather16_gbs", "smem_gather8_clk", "smem_gather16_clk",
+            "l1_gbs", "l2_gbs", "hbm_read_gbs")
+    return {k: round(c[k], 2) for k in keep}
+
+
+def hops_per_string(cl, n: int) -> float:
+    """Average hops of one spin string with n particles: a bond (i, j) moves a particle exactly when one
+    of its two sites is occupied, which 2 C(L-2, n-1) of the C(L, n) strings have."""
+    import math
+    if n <= 0 or n >= cl.L:
+        return 0.0
+    return len(cl.bonds) * 2 * math.comb(cl.L - 2, n - 1) / math.comb(cl.L, n)
+
+
+def onchip_roofline(cl, wk, dtype, cfg, pass_ms, ceil, D, hbm_peak):
+    """Rooflines of the two H·v passes against the measured on-chip ceilings.
+
+    Row pass: every spin-down hop of every state reads one vector element from the staged rows in
+    shared memory (z_dn elements per state); the ceiling is the conflict-free shared-memory load
+    rate (the random-gather rate is given beside it).  Spin-up pass: every spin-up hop reads one
+    element of a neighbouring row from L2 (z_up per state), plus y read and written once; the
+    ceiling is the L2 load rate."""
+    es = 4 if dtype == "f32" else 8
+    z_dn, z_up = hops_per_string(cl, wk["N_dn"]), hops_per_string(cl, wk["N_up"])
+    out = {"z_dn": round(z_dn, 3), "z_up": round(z_up, 3), "element_bytes": es}
+    if not cfg.get("split"):
+        out["note"] = "one-kernel form: no per-pass split"
+        return out
+    row_b = D * z_dn * es
+    up_b = D * (z_up * es + 2 * es)
+    r_gbs = row_b / (pass_ms["row_pass_ms"] * 1e-3) / 1e9
+    u_gbs = up_b / (pass_ms["up_pass_ms"] * 1e-3) / 1e9
+    out["row_pass"] = {"ms": pass_ms["row_pass_ms"], "bound": "shared memory", "bytes": int(row_b),
+                       "achieved_gbs": round(r_gbs, 1), "ceiling_gbs": ceil["smem_seq16_gbs"],
+                       "frac": round(r_gbs / ceil["smem_seq16_gbs"], 4),
+                       "random_gather16_gbs": ceil["smem_gather16_gbs"],
+                       "frac_vs_random_gather16": round(r_gbs / ceil["smem_gather16_gbs"], 4)}
+    out["up_pass"] = {"ms": pass_ms["up_pass_ms"], "bound": "L2", "bytes": int(up_b),
+                      "achieved_gbs": round(u_gbs, 1), "ceiling_gbs": ceil["l2_gbs"],
+                      "frac": round(u_gbs / ceil["l2_gbs"], 4)}
+    # the H·v can be no faster than both passes at their ceilings; the HBM fraction it would then reach
+    floor = row_b / (ceil["smem_seq16_gbs"] * 1e9) + up_b / (ceil["l2_gbs"] * 1e9)
+    out["hv_floor_ms"] = round(floor * 1e3, 4)
+    out["hbm_frac_at_floor"] = round(2 * es * D / floor / 1e9 / hbm_peak, 4)
     return out
 
 
@@ -757,9 +838,28 @@ def run_green(args, world, rank, local):
     h.close()
 
 
+def run_ceilings(args, local):
+    """The on-chip ceilings alone (one JSON line): the denominators of the H·v's on-chip rooflines."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1707_03974_gb300.build import build
+    build()
+    import paper_1707_03974_gb300 as pd
+    dev = torch.device("cuda", local)
+    runs = [measure_ceilings(pd, torch, dev) for _ in range(max(1, args.steps))]
+    best = {k: (min(r[k] for r in runs) if k.endswith("_clk") else max(r[k] for r in runs)) for k in runs[0]}
+    print(json.dumps({"metric": "measured on-chip ceilings", "unit": "mixed (see keys)", "n_gpus": 1,
+                      "runs": len(runs), "best": best, "all": runs,
+                      "gpu": torch.cuda.get_device_name(dev)}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.workload == "ceilings" and args.impl == "ours":
+        if rank == 0:
+            run_ceilings(args, local)
+        return
     if args.workload == "learned4x4" and args.impl == "ours":
         if rank == 0:
             run_learned(args, world, rank, local)

@@ -146,6 +146,16 @@ hb_status paradeisos_unrank(hb_handle h, const uint64_t *idx, uint64_t *states, 
  */
 hb_status hubbard_apply(hb_handle h, hb_dtype dt, const void *x, void *y, void *stream);
 
+/*
+ * hubbard_apply with a timing hook: records ev_begin, then the row pass
+ * (diagonal + spin-down hops) of the split form, ev_mid, the spin-up pass,
+ * ev_end, all on `stream` (cudaEvent_t passed as void*).  In the one-kernel
+ * form (and for momentum-sector handles) ev_mid and ev_end both follow the one
+ * kernel.  Same arguments, results and errors as hubbard_apply otherwise.
+ */
+hb_status hubbard_apply_timed(hb_handle h, hb_dtype dt, const void *x, void *y, void *ev_begin, void *ev_mid,
+                              void *ev_end, void *stream);
+
 /* Launch configuration of the H·v kernel for one vector type (zeros = library default). */
 typedef struct {
     int32_t rows_per_cta;     /* rows of x staged together in shared memory: 1, 2 or 4 (0 = widest that fits) */
@@ -278,14 +288,22 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
  * library, 2048 doubles (16 KiB), which every GPU that loads the library holds
  * until the process exits.
  *   - The caller still owns and passes v, vprev, w and the scalars.
+ *   - dt is HB_F64 or HB_F32.  HB_FX64 is refused with HB_ERR_INVALID_ARG: the
+ *     fixed-point step keeps three 128-bit partial sums per reduction block
+ *     (six doubles), which on a 152-SM GB300 is more than the array holds.
  *   - The handle's per-spin tables must already exist (any earlier
  *     hubbard_apply, hubbard_row_entries, lanczos_step or lanczos_ground_state
  *     on the handle builds them); otherwise HB_ERR_INVALID_STATE, because
- *     building them would allocate.
- *   - Call it with the handle's device current (else HB_ERR_INVALID_ARG).
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture begins.
+ *     building them would allocate.  Momentum-sector handles build theirs at
+ *     creation.
+ *   - Call it with the handle's device current (else HB_ERR_INVALID_ARG,
+ *     returned before anything is enqueued).
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current, so a device reset between calls leaves no
+ *     stale address behind.  With CUDA's lazy module loading the first call on
+ *     a device may make the driver load the library's device code, and that
+ *     load can allocate; make the first call before any stream capture begins
+ *     and before a strict memory budget takes effect.
  *   - A device whose reductions need more than 2048 partial sums (three per
  *     reduction block, four blocks per SM: more than 170 SMs) is rejected
  *     with HB_ERR_NO_MEMORY.
@@ -293,7 +311,8 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
  *     contents (nothing in it needs to start at zero: every slot is written
  *     before it is read).  Calls whose kernels overlap on the GPU race on it:
  *     serialise them (one stream, or events).
- * Neither this call nor anything it calls allocates or frees device memory.
+ * After the first call on a device, neither this call nor anything it calls
+ * allocates or frees device memory.
  */
 hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w,
                                const double *beta_prev, double *alpha, double *beta, void *ev_hv_begin,
@@ -403,6 +422,39 @@ hb_status paradeisos_inv_rank(hb_inv_handle h, const uint64_t *states, uint64_t 
 hb_status paradeisos_inv_unrank(hb_inv_handle h, const uint64_t *idx, uint64_t *states, uint64_t n_items, void *stream);
 /* Sticky error of the handle (synchronises the device, returns and clears it). */
 hb_status paradeisos_inv_last_error(hb_inv_handle h);
+
+/* ---------------- measured ceilings of the device (measurement support) ---------------- */
+
+/*
+ * The H·v of Eq. 1 reads 16 bytes per basis state from HBM but z hop operands
+ * per state through the SM's load path, so its rooflines include on-chip
+ * rates.  hb_measure_ceilings runs one small probe kernel per unit flat out
+ * on the current device and reports what it sustains (best of three launches,
+ * CUDA events).  Rates count useful work: flops (an FMA is 2), integer adds,
+ * or bytes delivered to registers.
+ */
+typedef struct {
+    int32_t sm_count;
+    double sm_clock_mhz;       /* SM cycles per global-timer nanosecond during the float32 probe */
+    double fp64_fma_tflops;    /* float64 FMA */
+    double fp32_fma_tflops;    /* float32 FMA */
+    double int32_add_tops;     /* 32-bit integer adds (10^12 per second) */
+    double int64_add_tops;     /* 64-bit integer adds (the fixed-point hop sums) */
+    double smem_seq16_gbs;     /* shared memory, conflict-free 16-byte loads (a warp reads 512 contiguous bytes) */
+    double smem_gather8_gbs;   /* shared memory, 8-byte loads at uniformly random addresses */
+    double smem_gather16_gbs;  /* shared memory, 16-byte loads at uniformly random addresses */
+    double smem_gather8_clk;   /* SM cycles per warp-wide random 8-byte gather (about its wavefronts) */
+    double smem_gather16_clk;  /* SM cycles per warp-wide random 16-byte gather */
+    double l1_gbs;             /* coalesced 16-byte global loads hitting L1 (16 KiB window per CTA) */
+    double l2_gbs;             /* coalesced 16-byte global loads served by L2 (window of l2_window_bytes) */
+    double hbm_read_gbs;       /* one streaming read pass over the buffer (0 if it is under 1 GiB) */
+    uint64_t l2_window_bytes, hbm_window_bytes;
+} hb_ceilings;
+
+/* buffer: caller-owned device memory of buffer_bytes >= 64 MiB, 16-byte aligned,
+ * overwritten (>= 1 GiB adds the HBM read probe).  Synchronises `stream`; takes
+ * well under a second. */
+hb_status hb_measure_ceilings(void *buffer, uint64_t buffer_bytes, hb_ceilings *out, void *stream);
 
 /*
  * Host utility (no GPU needed): lowest eigenvalue theta of the symmetric

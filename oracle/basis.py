@@ -86,6 +86,23 @@ def string_at(p: int, L: int, n: int) -> int:
     return s
 
 
+def next_string(s: int) -> int:
+    """The next larger integer with the same popcount (Sec. II A: advancing the
+    position p -> p + 1 of a spin string takes a few bit operations).
+
+    Gosper's successor (HAKMEM item 175, 1972): the lowest block of ones moves
+    its top bit one place up and the rest of the block to the bottom.  Unlike
+    count_below and string_at it counts nothing, so stepping with it checks
+    those two independently.
+    """
+    if s <= 0:
+        raise ValueError("need a positive string")
+    low = s & -s                # lowest set bit
+    ripple = s + low            # clears the lowest block of ones, sets the bit above it
+    ones = ((ripple ^ s) >> 2) // low  # the block's remaining ones, shifted to bit 0
+    return ripple | ones
+
+
 class Basis:
     """Full tensor-product basis of an (L, N_up, N_dn) sector, stored as a sorted list."""
 

@@ -10,7 +10,7 @@ def build(force: bool = False) -> str:
     src = os.path.join(HERE, "kron_hv.c")
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(src):
         return LIB
-    tmp = LIB + ".tmp"
+    tmp = f"{LIB}.{os.getpid()}.tmp"
     subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src])
     os.replace(tmp, LIB)
     return LIB

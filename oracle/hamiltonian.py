@@ -214,13 +214,11 @@ def spin_hop_matrix(L: int, n: int, bonds: np.ndarray, t: np.ndarray):
 
 
 def _load_c_helper():
-    """The OpenMP helper from oracle/kron_hv.c if it has been built, else None (numpy path)."""
+    """The OpenMP helper compiled from oracle/kron_hv.c (built here with gcc when absent or stale)."""
     import ctypes
-    import os
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liboracle_kron.so")
-    if not os.path.exists(path):
-        return None
-    lib = ctypes.CDLL(path)
+
+    from oracle.build import build
+    lib = ctypes.CDLL(build())
     lib.oracle_kron_apply.restype = None
     return lib
 
@@ -235,15 +233,22 @@ class KronOperator:
     the single-spin hopping matrices from `spin_hop_matrix`.  This is the same
     operator as `apply`, evaluated in an order that finishes on a laptop for
     D ~ 1e8; the tests pin it to `apply` and `row` on small clusters.
+
+    backend "c" evaluates the products in oracle/kron_hv.c (compiled on first
+    use; a failed build raises), "numpy" with scipy sparse products.  The
+    choice is explicit: nothing switches from one to the other on its own.
     """
 
-    def __init__(self, model: Model, use_c: bool = True):
+    def __init__(self, model: Model, backend: str = "c"):
+        if backend not in ("c", "numpy"):
+            raise ValueError("backend must be 'c' or 'numpy'")
         self.model = model
         self.A, self.up = spin_hop_matrix(model.L, model.N_up, model.bonds, model.t)
         self.B, self.dn = spin_hop_matrix(model.L, model.N_dn, model.bonds, model.t)
         self.D_up, self.D_dn = len(self.up), len(self.dn)
         self.D = self.D_up * self.D_dn
-        self._lib = _load_c_helper() if use_c else None
+        self.backend = backend
+        self._lib = _load_c_helper() if backend == "c" else None
         self._docc = None
 
     @property
@@ -262,21 +267,24 @@ class KronOperator:
         Y += (self.B @ X.T).T
         return Y.reshape(-1)
 
-    def _call_c(self, x):
+    def _call_c(self, x, absolute: bool = False):
         import ctypes
         y = np.empty_like(x)
         A, B = self.A, self.B
-        keep = [np.ascontiguousarray(a) for a in (A.indptr.astype(np.int64), A.indices.astype(np.int64), A.data,
-                                                  B.indptr.astype(np.int64), B.indices.astype(np.int64), B.data,
+        av, bv, U = (np.abs(A.data), np.abs(B.data), abs(self.model.U)) if absolute else (A.data, B.data, self.model.U)
+        keep = [np.ascontiguousarray(a) for a in (A.indptr.astype(np.int64), A.indices.astype(np.int64), av,
+                                                  B.indptr.astype(np.int64), B.indices.astype(np.int64), bv,
                                                   self.up, self.dn)]
         P = ctypes.c_void_p
         self._lib.oracle_kron_apply(ctypes.c_int64(self.D_up), ctypes.c_int64(self.D_dn),
-                                    *[P(k.ctypes.data) for k in keep], ctypes.c_double(self.model.U),
+                                    *[P(k.ctypes.data) for k in keep], ctypes.c_double(U),
                                     P(x.ctypes.data), P(y.ctypes.data))
         return y
 
     def abs_apply(self, x: np.ndarray) -> np.ndarray:
         """|H| |x| (entrywise absolute values): the scale of the rounding error of every row sum."""
+        if self._lib is not None:
+            return self._call_c(np.abs(np.ascontiguousarray(x, dtype=np.float64)), absolute=True)
         X = np.abs(np.asarray(x, dtype=np.float64)).reshape(self.D_up, self.D_dn)
         Y = abs(self.model.U) * self.docc * X
         Y += abs(self.A) @ X

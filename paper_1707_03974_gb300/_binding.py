@@ -54,6 +54,20 @@ class LanczosInfo(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class Ceilings(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int32), ("sm_clock_mhz", ctypes.c_double),
+                ("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
+                ("int32_add_tops", ctypes.c_double), ("int64_add_tops", ctypes.c_double),
+                ("smem_seq16_gbs", ctypes.c_double), ("smem_gather8_gbs", ctypes.c_double),
+                ("smem_gather16_gbs", ctypes.c_double), ("smem_gather8_clk", ctypes.c_double),
+                ("smem_gather16_clk", ctypes.c_double), ("l1_gbs", ctypes.c_double), ("l2_gbs", ctypes.c_double),
+                ("hbm_read_gbs", ctypes.c_double), ("l2_window_bytes", ctypes.c_uint64),
+                ("hbm_window_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def load():
     """Load libparadeisos.so (raises if it has not been built)."""
     global _lib
@@ -118,6 +132,8 @@ def load():
         "lanczos_step_scratch_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
         "lanczos_step": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, U64, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
         "lanczos_step_noalloc": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
+        "hb_measure_ceilings": (ctypes.c_int, [P, U64, ctypes.POINTER(Ceilings), P]),
+        "hubbard_apply_timed": (ctypes.c_int, [P, I32, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -317,6 +333,21 @@ def hubbard_apply(h: Handle, x, y=None, stream=None):
     if y.dtype != x.dtype or y.numel() != h.D:
         raise ValueError("y must match x in dtype and size")
     _check(load().hubbard_apply(h.ptr, _dtype_code(x), _ptr(x), _ptr(y), _stream_ptr(stream)), "hubbard_apply")
+    return y
+
+
+def hubbard_apply_timed(h: Handle, x, y, ev_begin, ev_mid, ev_end, stream=None):
+    """y = H x with CUDA events (torch.cuda.Event, timing enabled) recorded before the H·v, between its
+    row pass and spin-up pass (split form; after the kernel otherwise) and at the end."""
+    _need_cuda(x, y)
+    if x.numel() != h.D or y.numel() != h.D or y.dtype != x.dtype:
+        raise ValueError("x and y must have D elements of one dtype")
+    evs = []
+    for e in (ev_begin, ev_mid, ev_end):
+        e.record()  # materialise the event; the library re-records it on the stream
+        evs.append(ctypes.c_void_p(e.cuda_event))
+    _check(load().hubbard_apply_timed(h.ptr, _dtype_code(x), _ptr(x), _ptr(y), *evs, _stream_ptr(stream)),
+           "hubbard_apply_timed")
     return y
 
 
@@ -707,3 +738,12 @@ def hb_continued_fraction(alphas, betas, norm2: float, E0: float, z):
                                         float(norm2), float(E0), P(zr.ctypes.data), P(zi.ctypes.data), len(z),
                                         P(gr.ctypes.data), P(gi.ctypes.data)), "hb_continued_fraction")
     return gr + 1j * gi
+
+
+def hb_measure_ceilings(buffer, stream=None) -> dict:
+    """Measured on-chip rates of the current device; buffer: a CUDA tensor of at least 64 MiB (overwritten)."""
+    _need_cuda(buffer)
+    c = Ceilings()
+    _check(load().hb_measure_ceilings(_ptr(buffer), buffer.numel() * buffer.element_size(), ctypes.byref(c),
+                                      _stream_ptr(stream)), "hb_measure_ceilings")
+    return c.as_dict()

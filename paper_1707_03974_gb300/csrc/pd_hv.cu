@@ -578,3 +578,29 @@ extern "C" hb_status hubbard_apply(hb_handle h, hb_dtype dt, const void *x, void
     if (s != HB_OK) return s;
     return pd_apply(h, dt, x, y, reinterpret_cast<cudaStream_t>(stream));
 }
+
+extern "C" hb_status hubbard_apply_timed(hb_handle h, hb_dtype dt, const void *x, void *y, void *ev_begin,
+                                         void *ev_mid, void *ev_end, void *stream) {
+    if (!h || !x || !y || !ev_begin || !ev_mid || !ev_end || (dt != HB_F64 && dt != HB_F32 && dt != HB_FX64))
+        return HB_ERR_INVALID_ARG;
+    if (dt == HB_FX64 && !h->fx_ok) return HB_ERR_INVALID_ARG;
+    const size_t es = dt == HB_F32 ? 4 : 8;
+    const uintptr_t xb = (uintptr_t)x, yb = (uintptr_t)y, n = (uintptr_t)(h->D * es);
+    if (xb < yb + n && yb < xb + n) return HB_ERR_INVALID_ARG;
+    hb_status s = pd_build_tables(h);
+    if (s != HB_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = reinterpret_cast<cudaEvent_t>(ev_begin), e1 = reinterpret_cast<cudaEvent_t>(ev_mid),
+                e2 = reinterpret_cast<cudaEvent_t>(ev_end);
+    PD_CUDA(cudaEventRecord(e0, st));
+    if (h->ks || !h->hv_cfg[dt].split) {
+        if ((s = pd_apply(h, dt, x, y, st)) != HB_OK) return s;
+        PD_CUDA(cudaEventRecord(e1, st));
+    } else {
+        if ((s = apply_part(h, dt, x, y, st, kRowPass)) != HB_OK) return s;
+        PD_CUDA(cudaEventRecord(e1, st));
+        if ((s = apply_part(h, dt, x, y, st, kUpPass)) != HB_OK) return s;
+    }
+    PD_CUDA(cudaEventRecord(e2, st));
+    return HB_OK;
+}

@@ -1220,28 +1220,28 @@ hb_status lanczos_ritz_vector_f64(hb_handle h, const hb_lanczos_opts *o, const v
 // block (three for the float32 step's fused sums).  This variant keeps that scratch in a fixed file-scope device array,
 // so neither the library nor the caller allocates anything per call.  In host
 // code `g_noalloc_partials` names a host-side shadow, not device memory: its
-// device address is looked up once per device with cudaGetSymbolAddress and
-// cached below.  Every block of the two reductions overwrites its own slot
+// device address is looked up with cudaGetSymbolAddress on every call, with the
+// handle's device current, so a device or context reset between two calls can
+// never leave a stale address behind (the lookup costs about a microsecond once
+// the module is loaded).  Every block of the two reductions overwrites its own slot
 // before the final reduction reads it, so no slot has to start at zero; the
 // array simply keeps whatever the previous call left.  All calls on a device
 // share the array: two calls whose kernels overlap on the GPU race on it.
-#include <mutex>
+// The fixed-point step needs three 128-bit partials per block (six doubles),
+// more than the array holds on a GB300, so HB_FX64 is refused.
 
 #define PD_NOALLOC_PARTIALS 2048  // capacity: 2048 doubles = 16 KiB per device
-#define PD_NOALLOC_MAX_DEVICES 64
 
 static __device__ __align__(256) double g_noalloc_partials[PD_NOALLOC_PARTIALS];
-
-namespace {
-std::mutex g_noalloc_mutex;
-double *g_noalloc_dev_ptr[PD_NOALLOC_MAX_DEVICES] = {};
-}  // namespace
 
 extern "C" hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w,
                                           const double *beta_prev, double *alpha, double *beta, void *ev_hv_begin,
                                           void *ev_hv_end, uint32_t *launches, void *stream) {
     if (!h || !v || !w || !alpha || !beta || (dt != HB_F64 && dt != HB_F32)) return HB_ERR_INVALID_ARG;
     if ((vprev == nullptr) != (beta_prev == nullptr)) return HB_ERR_INVALID_ARG;
+    int dev = -1;
+    PD_CUDA(cudaGetDevice(&dev));
+    if (dev != h->device) return HB_ERR_INVALID_ARG;  // checked before anything is enqueued
     if (!h->tables_built) return HB_ERR_INVALID_STATE;  // building them would allocate
     const size_t es = dt == HB_F64 ? 8 : 4;
     const uintptr_t n = (uintptr_t)(h->D * es), wb = (uintptr_t)w;
@@ -1249,27 +1249,16 @@ extern "C" hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *
         const uintptr_t pb = (uintptr_t)p;
         if (p && pb < wb + n && wb < pb + n) return HB_ERR_INVALID_ARG;
     }
-    int dev = -1;
-    PD_CUDA(cudaGetDevice(&dev));
-    if (dev != h->device || dev < 0 || dev >= PD_NOALLOC_MAX_DEVICES) return HB_ERR_INVALID_ARG;
     const uint64_t nblk = (uint64_t)step_blocks(h);  // up to three float64 partials per block are used here
     if (3 * nblk > PD_NOALLOC_PARTIALS) return HB_ERR_NO_MEMORY;  // device wider than the fixed scratch
-    double *partials = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_dev_ptr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return HB_ERR_CUDA;
-            g_noalloc_dev_ptr[dev] = static_cast<double *>(p);
-        }
-        partials = g_noalloc_dev_ptr[dev];
-    }
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return HB_ERR_CUDA;
     Solve s;
     s.h = h;
     s.st = reinterpret_cast<cudaStream_t>(stream);
     s.D = h->D;
     s.nblk = (int)nblk;
-    s.partials = partials;
+    s.partials = static_cast<double *>(p);
     s.grid_vec = h->sm_count * 8;
     cudaEvent_t e0 = reinterpret_cast<cudaEvent_t>(ev_hv_begin), e1 = reinterpret_cast<cudaEvent_t>(ev_hv_end);
     hb_status st;

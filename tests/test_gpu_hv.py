@@ -33,7 +33,7 @@ def env():
 
 def abs_bound(m, b, x):
     """sum_c |H_rc x_c| for every row (the |H| |x| product), from the oracle."""
-    return KronOperator(m, use_c=False).abs_apply(x)
+    return KronOperator(m, backend="numpy").abs_apply(x)
 
 
 CASES = [(wl.ring(8), 4, 4, 4.0), (wl.ring(8), 3, 5, 1.0), (wl.ring(6), 2, 3, 2.5), (wl.dimer(), 1, 1, 4.0),
@@ -155,6 +155,59 @@ def test_hv_square4x4_full_vector_vs_tensor_product_oracle(env, square4x4):
     h = handle_for(cl, 8.0, 8, 8)
     y = pd.hubbard_apply(h, torch.from_numpy(x).cuda()).cpu().numpy()
     assert np.max(np.abs(y - yr)) <= 1e-12 * np.max(np.abs(yr))
+    h.close()
+
+
+# The split launch configuration the autotuner picks for fixed-point vectors on
+# the 4x4 benchmark workload (and which bench.py then times).
+BENCH_SPLIT_FX = {"rows_per_cta": 2, "threads_per_cta": 1024, "visit_order": 0, "split": 1, "up_block": 128,
+                  "up_threads": 512, "up_rows": 4}
+BENCH_SPLIT_F32 = {"rows_per_cta": 4, "threads_per_cta": 1024, "visit_order": 0, "split": 1, "up_block": 128,
+                   "up_threads": 512, "up_rows": 4}
+
+
+@pytest.mark.parametrize("dtype", ["fx64", "f32"])
+def test_hv_square4x4_bench_split_config_full_vector(env, square4x4, dtype):
+    """D = 165,636,900, the split H·v in the configuration the benchmark runs
+    (and in whatever the autotuner picks on this GPU): every element of y
+    against the oracle's tensor-product operator (C helper) applied to the same
+    input, within the rounding bound of each vector type."""
+    torch, pd = env
+    cl, m, b = square4x4
+    k = KronOperator(m)
+    assert k._lib is not None
+    h = handle_for(cl, 8.0, 8, 8)
+    x = start_vector(9, b.D)
+    xt = torch.from_numpy(x).cuda()
+    if dtype == "fx64":
+        F = pd.hubbard_fixed_point_bits(h)
+        xin = pd.hubbard_convert(h, xt, torch.int64)
+        xref = np.ldexp(xin.cpu().numpy().astype(np.float64), -F)
+        tdt, cfg = torch.int64, BENCH_SPLIT_FX
+    else:
+        xin = xt.float()
+        xref = xin.cpu().numpy().astype(np.float64)
+        tdt, cfg = torch.float32, BENCH_SPLIT_F32
+    del xt
+    yr = k(xref)
+    habs = k.abs_apply(xref)
+    n_classes = len(set(cl.t))
+    bound = (n_classes + 2) * 2.0 ** -F + 64 * EPS64 * habs if dtype == "fx64" else 64 * EPS32 * habs + 1e-30
+    del habs
+    y = torch.empty_like(xin)
+    tuned = pd.hubbard_autotune(h, xin, y, reps=1)
+    configs = [cfg] + ([tuned] if tuned.get("split") else [])
+    for c in configs:
+        pd.hubbard_set_hv_config(h, tdt, **{key: c[key] for key in BENCH_SPLIT_FX})
+        pd.hubbard_apply(h, xin, y)
+        if dtype == "fx64":
+            yd = np.ldexp(y.cpu().numpy().astype(np.float64), -F)
+        else:
+            yd = y.cpu().numpy().astype(np.float64)
+        bad = np.count_nonzero(np.abs(yd - yr) > bound)
+        assert bad == 0, (c, bad)
+        del yd
+    assert pd.hubbard_last_error(h) == "HB_OK"
     h.close()
 
 

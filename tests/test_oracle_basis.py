@@ -6,7 +6,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle.basis import Basis, count_below, position, spin_list, string_at
+from oracle.basis import Basis, count_below, next_string, position, spin_list, string_at
 from tests.conftest import GOLDEN
 
 EX = json.load(open(os.path.join(GOLDEN, "paper_examples.json")))
@@ -49,6 +49,38 @@ def test_count_below_equals_sorted_position(L):
             s = int(lst[p])
             assert count_below(s, L, n) == p
             assert string_at(p, L, n) == s
+
+
+@pytest.mark.parametrize("L", range(1, 15))
+def test_next_string_walks_the_sorted_list(L):
+    """The bit-operation successor (Sec. II A) visits the sorted list in order."""
+    for n in range(1, L + 1):
+        lst = spin_list(L, n)
+        for a, b in zip(lst[:-1], lst[1:]):
+            assert next_string(int(a)) == int(b)
+        assert next_string(int(lst[-1])) >> L  # past the last string the successor leaves L bits
+
+
+@pytest.mark.parametrize("L,n", [(32, 16), (32, 1), (32, 31), (31, 9), (24, 12), (28, 5)])
+def test_count_below_steps_by_one_at_large_L(L, n):
+    """Above the enumerable sizes: walking with the successor, which counts
+    nothing, count_below must grow by exactly one per step and string_at must
+    return the walked string -- from the first string, around a random interior
+    position and up to the last string."""
+    D = math.comb(L, n)
+    rng = np.random.default_rng(L * 100 + n)
+    starts = [0, max(0, D - 1500)] + ([int(rng.integers(1500, D - 3000))] if D > 6000 else [])
+    for p0 in starts:
+        s = string_at(p0, L, n)
+        assert count_below(s, L, n) == p0
+        p = p0
+        for _ in range(min(1499, D - 1 - p0)):
+            s = next_string(s)
+            p += 1
+            assert count_below(s, L, n) == p
+            assert string_at(p, L, n) == s
+    assert string_at(0, L, n) == (1 << n) - 1
+    assert string_at(D - 1, L, n) == ((1 << n) - 1) << (L - n)
 
 
 def test_count_below_edge_sectors():

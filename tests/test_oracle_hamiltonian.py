@@ -80,12 +80,17 @@ def test_row_count_is_one_plus_hops():
 @pytest.mark.parametrize("cl,nu,nd,U", [(wl.ring(8), 4, 4, 4.0), (wl.ring(7), 3, 2, 2.0),
                                         (wl.rect_periodic(4, 3), 3, 4, 5.0),
                                         (wl.rect_periodic(3, 3, 1.0, -0.3), 4, 4, 8.0)])
-def test_apply_matches_dense_and_kron(cl, nu, nd, U):
+@pytest.mark.parametrize("backend", ["c", "numpy"])
+def test_apply_matches_dense_and_kron(cl, nu, nd, U, backend):
+    """Both evaluations of the tensor-product form (the C helper of
+    oracle/kron_hv.c, which the full-size GPU checks and the CPU baseline use,
+    and the scipy one) against the term-by-term definition and the dense matrix."""
     m = Model.from_cluster(cl, U, nu, nd)
     b = Basis(cl.L, nu, nd)
     x = start_vector(3, b.D)
     y = apply(m, b, x)
-    k = KronOperator(m)
+    k = KronOperator(m, backend=backend)
+    assert (k._lib is not None) == (backend == "c")
     yk = k(x)
     assert np.max(np.abs(y - yk)) <= 1e-13 * np.max(np.abs(y))
     if b.D <= 6000:
@@ -112,13 +117,14 @@ def test_basis_vector_gives_row():
         assert np.array_equal(col[nz], vals)
 
 
-def test_abs_apply_is_entrywise_absolute_product():
+@pytest.mark.parametrize("backend", ["c", "numpy"])
+def test_abs_apply_is_entrywise_absolute_product(backend):
     cl = wl.rect_periodic(3, 3, 1.0, -0.3)
-    m = Model.from_cluster(cl, 3.0, 4, 3)
+    m = Model.from_cluster(cl, -3.0, 4, 3)  # negative U: the absolute value must reach the diagonal too
     b = Basis(9, 4, 3)
     x = start_vector(2, b.D)
     want = np.abs(dense(m, b)) @ np.abs(x) if b.D <= 6000 else None
-    got = KronOperator(m, use_c=False).abs_apply(x)
+    got = KronOperator(m, backend=backend).abs_apply(x)
     if want is None:
         # row by row from the canonical rows
         for r in range(0, b.D, 997):
