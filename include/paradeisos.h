@@ -353,14 +353,38 @@ hb_status lanczos_batch_workspace_bytes(hb_batch_handle b, const hb_lanczos_opts
 /*
  * Lowest eigenvalue of every instance by the three-term Lanczos recurrence
  * (vec_dtype HB_F64 or HB_FX64; reorth and fp64_finish are not supported).
- * Instance k starts from the SplitMix64 vector of seed opts->seed + k.  One
- * step of all instances is captured once into a CUDA graph (per slot phase)
- * and replayed; every check_every steps the host solves each instance's
- * tridiagonal, and converged instances are masked out of later steps.
+ * Instance k starts from the SplitMix64 vector of seed opts->seed + k.
+ * All steps of all instances run in one persistent cooperative kernel: per
+ * step, the H·v of every row group of every active instance fused with
+ * w = H v - beta vprev and the step's reductions, a grid barrier, then alpha
+ * and beta of every instance (fixed point: from exact 128-bit sums in
+ * double-double) and the vector update, and another barrier (float64 takes a
+ * third phase for its second reduction).  Every check_every steps the CTA
+ * holding an instance's first element solves its tridiagonal on the device
+ * (Sturm multisection, inverse iteration) and masks it once
+ * beta_j |s_last| <= tol max(1, |theta|).  One launch runs up to 64 steps and
+ * is replayed from a captured CUDA graph until all instances have converged
+ * or maxit is reached; the final E0 and residuals come from the recorded
+ * coefficients through hb_tridiag_lowest.  Every grid barrier's wait gives up
+ * after 5 s (global timer, with a poll cap); the call then returns
+ * HB_ERR_TIMEOUT and the context stays usable.  A device without cooperative
+ * launch support gives HB_ERR_CUDA.
  * E0, info: HOST arrays [n].  Synchronises `stream`.
  */
 hb_status lanczos_batch_ground_state(hb_batch_handle b, const hb_lanczos_opts *opts, void *workspace,
                                      uint64_t workspace_bytes, double *E0, hb_lanczos_info *info, void *stream);
+
+/*
+ * Self-test of the bounded waits of lanczos_batch_ground_state: runs its first
+ * step with CTA withhold_cta leaving the kernel before its first arrival at a
+ * grid barrier, and a wait limit of limit_ms (1 .. 10000).  The other CTAs'
+ * waits give up, so the expected result is HB_ERR_TIMEOUT, after which the
+ * batch and the device remain usable.  Same workspace as
+ * lanczos_batch_ground_state.  Synchronises `stream`.
+ */
+hb_status lanczos_batch_wait_selftest(hb_batch_handle b, const hb_lanczos_opts *opts, void *workspace,
+                                      uint64_t workspace_bytes, int32_t withhold_cta, uint32_t limit_ms,
+                                      void *stream);
 
 /* ---------------- dynamical response (the continued fraction named in Sec. I) ---------------- */
 

@@ -125,6 +125,8 @@ def load():
         "hubbard_batch_autotune": (ctypes.c_int, [P, I32, P, P, I32, ctypes.POINTER(HvConfig), P]),
         "lanczos_batch_workspace_bytes": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), ctypes.POINTER(U64)]),
         "lanczos_batch_ground_state": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, U64, P, P, P]),
+        "lanczos_batch_wait_selftest": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, U64, ctypes.c_int32,
+                                                       ctypes.c_uint32, P]),
         "hubbard_get_hv_config": (ctypes.c_int, [P, I32, ctypes.POINTER(HvConfig)]),
         "hubbard_set_hv_config": (ctypes.c_int, [P, I32, ctypes.POINTER(HvConfig)]),
         "hubbard_autotune": (ctypes.c_int, [P, I32, P, P, I32, ctypes.POINTER(HvConfig), P]),
@@ -553,6 +555,20 @@ def lanczos_batch_ground_state(b: Batch, maxit: int = 1000, tol: float = 1e-10, 
         raise HubbardError(st, "lanczos_batch_ground_state")
     return E0.tolist(), [{"E0": i.E0, "residual": i.residual, "iterations": i.iterations,
                           "converged": bool(i.converged), "seconds": i.seconds} for i in infos], STATUS[st]
+
+
+def lanczos_batch_wait_selftest(b: Batch, withhold_cta: int = 0, limit_ms: int = 50, dtype=None, stream=None) -> str:
+    """One batched step with CTA `withhold_cta` never arriving at the first grid barrier: the other
+    CTAs' bounded waits must give up (expected "HB_ERR_TIMEOUT")."""
+    import torch
+    dt = {None: HB_FX64, torch.float64: HB_F64, torch.int64: HB_FX64}[dtype]
+    o = LanczosOpts(4, 0, dt, 1, 1e-10, 0, 0, 0)
+    lib = load()
+    nb = ctypes.c_uint64()
+    _check(lib.lanczos_batch_workspace_bytes(b._b, ctypes.byref(o), ctypes.byref(nb)), "lanczos_batch_workspace_bytes")
+    ws = torch.empty((nb.value,), dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+    return STATUS[lib.lanczos_batch_wait_selftest(b._b, ctypes.byref(o), _ptr(ws), nb.value, int(withhold_cta),
+                                                  int(limit_ms), _stream_ptr(stream))]
 
 
 # ---------------------------------------------------------------- learned start vector (paradeisos_mlp.h)

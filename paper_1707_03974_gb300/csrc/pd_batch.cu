@@ -1,6 +1,7 @@
 // Batched Hubbard problems: many clusters / sectors / U values of uneven
-// dimension in single launches, and a batched Lanczos whose steps are replayed
-// from a captured CUDA graph.
+// dimension in single launches, and a batched Lanczos run by one persistent
+// cooperative kernel (grid barriers whose waits give up after a limit), whose
+// chunks of steps are replayed from a captured CUDA graph.
 //
 // The paper's method per instance is unchanged (Eq. 1 with Paradeisos-ranked
 // hop tables, Eq. 3); the batch only concatenates the instances' vectors and
@@ -11,6 +12,10 @@
 #include <new>
 #include <vector>
 
+#include <cfloat>
+#include <type_traits>
+
+#include "pd_exact.cuh"
 #include "pd_hv_body.cuh"
 
 namespace {
@@ -49,7 +54,8 @@ template <int R, int MODE, int NC>
 __global__ void __launch_bounds__(512) k_batch_hv(const Inst *__restrict__ inst, const uint64_t *__restrict__ prefix,
                                                   int n, const int *__restrict__ active, const void *x, void *y) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Inst s_inst;
+    __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];  // filled by copy_inst, no constructor
+    Inst &s_inst = *reinterpret_cast<Inst *>(s_inst_raw);
     __shared__ int s_k;
     const uint64_t total = prefix[n];
     int cur = -1;
@@ -79,212 +85,24 @@ __global__ void __launch_bounds__(512) k_batch_hv(const Inst *__restrict__ inst,
     }
 }
 
-// ---------------- batched vector kernels (grid: x = blocks per instance, y = instance) ----------------
-struct I128 {
-    uint64_t lo = 0;
-    int64_t hi = 0;
-};
-__device__ __forceinline__ void i128_add(I128 &s, const I128 &t) {
-    const uint64_t lo = s.lo + t.lo;
-    s.hi += t.hi + (lo < t.lo ? 1 : 0);
-    s.lo = lo;
-}
-__device__ __forceinline__ void i128_add_prod(I128 &s, int64_t a, int64_t b, int sh) {
-    const int64_t ph = __mul64hi(a, b);
-    const uint64_t pl = (uint64_t)a * (uint64_t)b;
-    I128 p;
-    p.lo = sh == 0 ? pl : ((pl >> sh) | ((uint64_t)ph << (64 - sh)));
-    p.hi = sh == 0 ? ph : (ph >> sh);
-    i128_add(s, p);
-}
-__device__ __forceinline__ I128 block_sum128(I128 v) {
-    __shared__ uint64_t s_lo[32];
-    __shared__ int64_t s_hi[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        I128 t;
-        t.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
-        t.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
-        i128_add(v, t);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) {
-        s_lo[wid] = v.lo;
-        s_hi[wid] = v.hi;
-    }
-    __syncthreads();
-    I128 r;
-    if (wid == 0) {
-        if (lane < (int)((blockDim.x + 31) >> 5)) {
-            r.lo = s_lo[lane];
-            r.hi = s_hi[lane];
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            I128 t;
-            t.lo = __shfl_down_sync(0xffffffffu, r.lo, o);
-            t.hi = __shfl_down_sync(0xffffffffu, r.hi, o);
-            i128_add(r, t);
-        }
-    }
-    return r;
-}
-__device__ __forceinline__ double block_sum_d(double v) {
-    __shared__ double s_w[32];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) s_w[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (wid == 0) {
-        r = lane < (int)((blockDim.x + 31) >> 5) ? s_w[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-    }
-    return r;
-}
+// ---------------- batched Lanczos: one persistent kernel for all instances ----------------
+using pdx::block_sum128;
+using pdx::block_sum_d;
+using pdx::I128;
+using pdx::i128_add;
+using pdx::i128_add_prod;
 
-// Per-step state on the device: the step counter j (slots and alpha/beta
-// entries are derived from it), so the same captured graph replays every step.
-struct BState {
+// Start vectors (instance k: SplitMix64 seeded with seed + k, normalised).
+// Grid: x = blocks per instance, y = instance.
+struct StartState {
     const Inst *inst;
-    const int *active;
-    const int *j;         // current step
-    uint64_t stride;      // elements per slot (whole batch vector)
-    int n, maxit1, nb;
-    void *V;              // 3 slots
-    I128 *part;           // [n][nb] (float64 runs use the lo word as a double)
-    double *alpha, *beta; // [n][maxit1]
+    void *V;    // slot 0 of the batch vector
+    I128 *part; // [n][nb]
+    int nb;
 };
 
 template <bool FX>
-__global__ void k_b_axpy_dot(BState s) {
-    const int k = blockIdx.y;
-    if (!s.active[k]) return;
-    const int j = *s.j;
-    const Inst &in = s.inst[k];
-    const uint64_t D = in.D;
-    const int iv = j % 3, ip = (j + 2) % 3, iw = (j + 1) % 3;
-    const double bprev = j > 0 ? s.beta[k * s.maxit1 + j - 1] : 0.0;
-    if (FX) {
-        int64_t *V = static_cast<int64_t *>(s.V);
-        int64_t *w = V + iw * s.stride + in.off;
-        const int64_t *v = V + iv * s.stride + in.off, *vp = V + ip * s.stride + in.off;
-        const FxCoef b = fx_coef_dev(bprev);
-        I128 acc;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < D; i += (uint64_t)gridDim.x * blockDim.x) {
-            int64_t wi = w[i];
-            if (j > 0) {
-                wi -= fx_mul(vp[i], b.K, b.G);
-                w[i] = wi;
-            }
-            i128_add_prod(acc, wi, v[i], 0);
-        }
-        const I128 t = block_sum128(acc);
-        if (threadIdx.x == 0) s.part[k * s.nb + blockIdx.x] = t;
-    } else {
-        double *V = static_cast<double *>(s.V);
-        double *w = V + iw * s.stride + in.off;
-        const double *v = V + iv * s.stride + in.off, *vp = V + ip * s.stride + in.off;
-        double acc = 0.0;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < D; i += (uint64_t)gridDim.x * blockDim.x) {
-            double wi = w[i];
-            if (j > 0) {
-                wi = wi - bprev * vp[i];
-                w[i] = wi;
-            }
-            acc = fma(wi, v[i], acc);
-        }
-        const double t = block_sum_d(acc);
-        if (threadIdx.x == 0) reinterpret_cast<double *>(s.part)[2 * (k * s.nb + blockIdx.x)] = t;
-    }
-}
-
-template <bool FX>
-__global__ void k_b_axpy_norm(BState s) {
-    const int k = blockIdx.y;
-    if (!s.active[k]) return;
-    const int j = *s.j;
-    const Inst &in = s.inst[k];
-    const uint64_t D = in.D;
-    const int iv = j % 3, iw = (j + 1) % 3;
-    const double al = s.alpha[k * s.maxit1 + j];
-    if (FX) {
-        int64_t *V = static_cast<int64_t *>(s.V);
-        int64_t *w = V + iw * s.stride + in.off;
-        const int64_t *v = V + iv * s.stride + in.off;
-        const FxCoef a = fx_coef_dev(al);
-        I128 acc;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < D; i += (uint64_t)gridDim.x * blockDim.x) {
-            const int64_t wi = w[i] - fx_mul(v[i], a.K, a.G);
-            w[i] = wi;
-            i128_add_prod(acc, wi, wi, 0);
-        }
-        const I128 t = block_sum128(acc);
-        if (threadIdx.x == 0) s.part[k * s.nb + blockIdx.x] = t;
-    } else {
-        double *V = static_cast<double *>(s.V);
-        double *w = V + iw * s.stride + in.off;
-        const double *v = V + iv * s.stride + in.off;
-        double acc = 0.0;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < D; i += (uint64_t)gridDim.x * blockDim.x) {
-            const double wi = w[i] - al * v[i];
-            w[i] = wi;
-            acc = fma(wi, wi, acc);
-        }
-        const double t = block_sum_d(acc);
-        if (threadIdx.x == 0) reinterpret_cast<double *>(s.part)[2 * (k * s.nb + blockIdx.x)] = t;
-    }
-}
-
-// which: 0 -> alpha[k][j] = sum, 1 -> beta[k][j] = sqrt(sum)
-template <bool FX>
-__global__ void k_b_reduce(BState s, int which) {
-    const int k = blockIdx.x;
-    if (!s.active[k]) return;
-    const int j = *s.j;
-    double v;
-    if (FX) {
-        I128 acc;
-        for (int i = threadIdx.x; i < s.nb; i += blockDim.x) i128_add(acc, s.part[k * s.nb + i]);
-        acc = block_sum128(acc);
-        v = ldexp((double)acc.hi * 18446744073709551616.0 + (double)acc.lo, -2 * s.inst[k].F);
-    } else {
-        double acc = 0.0;
-        for (int i = threadIdx.x; i < s.nb; i += blockDim.x) acc += reinterpret_cast<const double *>(s.part)[2 * (k * s.nb + i)];
-        v = block_sum_d(acc);
-    }
-    if (threadIdx.x == 0) {
-        if (which == 0) s.alpha[k * s.maxit1 + j] = v;
-        else s.beta[k * s.maxit1 + j] = sqrt(v);
-    }
-}
-
-template <bool FX>
-__global__ void k_b_scale(BState s) {
-    const int k = blockIdx.y;
-    if (!s.active[k]) return;
-    const int j = *s.j;
-    const Inst &in = s.inst[k];
-    const double b = s.beta[k * s.maxit1 + j];
-    const double f = b != 0.0 ? 1.0 / b : 0.0;
-    const int iw = (j + 1) % 3;
-    if (FX) {
-        int64_t *w = static_cast<int64_t *>(s.V) + iw * s.stride + in.off;
-        const FxCoef c = fx_coef_dev(f);
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < in.D; i += (uint64_t)gridDim.x * blockDim.x)
-            w[i] = fx_mul(w[i], c.K, c.G);
-    } else {
-        double *w = static_cast<double *>(s.V) + iw * s.stride + in.off;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < in.D; i += (uint64_t)gridDim.x * blockDim.x)
-            w[i] *= f;
-    }
-}
-
-__global__ void k_b_advance(int *j) { *j += 1; }
-
-// start vectors: instance k uses SplitMix64 seeded with seed + k; then normalised
-template <bool FX>
-__global__ void k_b_fill(BState s, uint64_t seed) {
+__global__ void k_b_fill(StartState s, uint64_t seed) {
     const int k = blockIdx.y;
     const Inst &in = s.inst[k];
     const uint64_t sk = seed + (uint64_t)k;
@@ -306,14 +124,14 @@ __global__ void k_b_fill(BState s, uint64_t seed) {
 }
 
 template <bool FX>
-__global__ void k_b_norm_partials(BState s) {
+__global__ void k_b_norm_partials(StartState s) {
     const int k = blockIdx.y;
     const Inst &in = s.inst[k];
     if (FX) {
         const int64_t *v = static_cast<const int64_t *>(s.V) + in.off;
         I128 acc;
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < in.D; i += (uint64_t)gridDim.x * blockDim.x)
-            i128_add_prod(acc, v[i], v[i], 0);
+            i128_add_prod(acc, v[i], v[i]);
         const I128 t = block_sum128(acc);
         if (threadIdx.x == 0) s.part[k * s.nb + blockIdx.x] = t;
     } else {
@@ -328,7 +146,7 @@ __global__ void k_b_norm_partials(BState s) {
 
 // slot 0 of instance k *= 1 / sqrt(sum of its partials)
 template <bool FX>
-__global__ void k_b_normalise(BState s) {
+__global__ void k_b_normalise(StartState s) {
     const int k = blockIdx.x;
     const Inst &in = s.inst[k];
     __shared__ double s_f;
@@ -356,10 +174,457 @@ __global__ void k_b_normalise(BState s) {
     }
 }
 
-uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
-void tridiag_lowest(const double *a, const double *b, int n, double *theta, double *s_last) {
-    hb_tridiag_lowest(a, b, n, theta, s_last);
+// ---- bounded grid barrier ----
+// All CTAs of a cooperative launch meet here.  A CTA whose wait exceeds
+// limit_ns (measured on the global nanosecond timer; a poll count caps it as
+// well) raises `abort` and records where; every CTA then leaves the kernel at
+// its next barrier, so nothing waits forever and the host reads HB_ERR_TIMEOUT.
+struct GridSync {
+    unsigned count;  // arrivals in the current generation
+    unsigned gen;    // generation, bumped by the last arrival
+    unsigned abort;  // 1 once a wait gave up
+    unsigned where;  // 1 + index of the barrier that gave up
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(GridSync *gs, unsigned long long limit_ns, unsigned tag) {
+    __shared__ int s_ok;
+    __syncthreads();  // the CTA's work of this phase is done
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire(&gs->gen);
+        __threadfence();  // this CTA's writes are visible before its arrival counts
+        if (atomicAdd(&gs->count, 1u) == gridDim.x - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            st_release(&gs->gen, g + 1);
+        } else {
+            const unsigned long long t0 = global_ns();
+            const unsigned long long max_polls = (limit_ns >> 5) + 1024;
+            for (unsigned long long polls = 0; ld_acquire(&gs->gen) == g; ++polls) {
+                if (ld_acquire(&gs->abort)) {
+                    ok = 0;
+                    break;
+                }
+                if (polls >= max_polls || global_ns() - t0 > limit_ns) {
+                    atomicExch(&gs->where, tag + 1);
+                    atomicExch(&gs->abort, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (ok && ld_acquire(&gs->abort)) ok = 0;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---- lowest eigenpair of the Lanczos tridiagonal, on the device (one warp) ----
+__device__ int sturm_below_dev(const double *a, const double *b, int n, double x) {
+    int c = 0;
+    double q = 1.0;
+    for (int i = 0; i < n; ++i) {
+        const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+        q = (a[i] - x) - (i > 0 ? bb / q : 0.0);
+        if (q == 0.0) q = -DBL_EPSILON * (fabs(a[i]) + fabs(x) + DBL_MIN);
+        if (q < 0.0) ++c;
+    }
+    return c;
+}
+
+// (T - theta I) z = z in place, Gaussian elimination with partial pivoting on
+// the tridiagonal (row interchanges as in LAPACK's gttrf); ws: 5 n doubles.
+__device__ void shifted_solve_dev(const double *a, const double *b, int n, double theta, double *z, double *ws) {
+    double *dl = ws, *d = ws + n, *du = ws + 2 * n, *du2 = ws + 3 * n;
+    double scale = 0.0;
+    for (int i = 0; i < n; ++i) {
+        d[i] = a[i] - theta;
+        scale = fmax(scale, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0));
+    }
+    for (int i = 0; i + 1 < n; ++i) dl[i] = du[i] = b[i];
+    const double tiny = DBL_EPSILON * (scale > 0 ? scale : 1.0);
+    double *swapped = ws + 4 * n;  // 1.0 where rows i and i+1 were interchanged
+    for (int i = 0; i + 1 < n; ++i) {
+        if (fabs(d[i]) >= fabs(dl[i])) {
+            if (d[i] == 0.0) d[i] = tiny;
+            const double f = dl[i] / d[i];
+            dl[i] = f;
+            d[i + 1] -= f * du[i];
+            if (i + 2 < n) du2[i] = 0.0;
+            swapped[i] = 0.0;
+        } else {
+            const double f = d[i] / dl[i];
+            d[i] = dl[i];
+            dl[i] = f;
+            const double tmp = du[i];
+            du[i] = d[i + 1];
+            d[i + 1] = tmp - f * d[i + 1];
+            if (i + 2 < n) {
+                du2[i] = du[i + 1];
+                du[i + 1] = -f * du[i + 1];
+            }
+            swapped[i] = 1.0;
+        }
+    }
+    if (d[n - 1] == 0.0) d[n - 1] = tiny;
+    for (int i = 0; i + 1 < n; ++i) {
+        if (swapped[i] == 0.0) {
+            z[i + 1] -= dl[i] * z[i];
+        } else {
+            const double tmp = z[i];
+            z[i] = z[i + 1];
+            z[i + 1] = tmp - dl[i] * z[i];
+        }
+    }
+    z[n - 1] /= d[n - 1];
+    if (n > 1) z[n - 2] = (z[n - 2] - du[n - 2] * z[n - 1]) / d[n - 2];
+    for (int i = n - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / d[i];
+}
+
+// theta = lowest eigenvalue of T_n (alpha a[0..n), beta b[0..n-1)) by multisection:
+// the 32 lanes count the eigenvalues below 32 points of the bracket with the
+// Sturm sequence, and the bracket shrinks to the two points around the first
+// count >= 1, until it stops shrinking.  s_last: last component of the
+// normalised eigenvector by three steps of inverse iteration from all ones
+// (lane 0; ws: 6 n doubles).  Called by all 32 lanes of one warp.
+__device__ void tri_lowest_warp(const double *a, const double *b, int n, double *ws, double *theta,
+                                double *s_last) {
+    const int lane = threadIdx.x & 31;
+    if (n == 1) {
+        *theta = a[0];
+        *s_last = 1.0;
+        return;
+    }
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = lane; i < n; i += 32) {
+        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0);
+        lo = fmin(lo, a[i] - r);
+        hi = fmax(hi, a[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    for (int round = 0; round < 64; ++round) {
+        const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
+        const unsigned m = __ballot_sync(0xffffffffu, sturm_below_dev(a, b, n, x) >= 1);
+        double nlo, nhi;
+        if (m == 0) {
+            nlo = __shfl_sync(0xffffffffu, x, 31);
+            nhi = hi;
+        } else {
+            const int f = __ffs(m) - 1;
+            nhi = __shfl_sync(0xffffffffu, x, f);
+            const double xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+            nlo = f > 0 ? xp : lo;
+        }
+        if (!(nhi - nlo < hi - lo)) break;  // no progress: the bracket is a few doubles wide
+        lo = fmax(lo, nlo);
+        hi = fmin(hi, nhi);
+        if (!(lo < hi)) break;
+    }
+    const double th = 0.5 * (lo + hi);
+    if (lane == 0) {
+        double *z = ws + 5 * n;
+        for (int i = 0; i < n; ++i) z[i] = 1.0;
+        for (int it = 0; it < 3; ++it) {
+            shifted_solve_dev(a, b, n, th, z, ws);
+            double nrm = 0.0;
+            for (int i = 0; i < n; ++i) nrm += z[i] * z[i];
+            nrm = sqrt(nrm);
+            if (!(nrm > 0.0) || !isfinite(nrm)) break;
+            for (int i = 0; i < n; ++i) z[i] /= nrm;
+        }
+        *theta = th;
+        *s_last = z[n - 1];
+    }
+}
+
+// ---- the persistent kernel ----
+struct PState {
+    const Inst *inst;
+    const uint64_t *prefix;  // [n+1] prefix sums of row groups (items)
+    int n;
+    int *active;             // [n]
+    int *jdev;               // step index, carried across launches
+    int *n_active;           // active instances after the launch
+    int chunk, maxit, maxit1, check_every;
+    double tol;
+    uint64_t stride;         // elements per vector slot
+    uint64_t total;          // elements of one batch vector (instance k at [off_k, off_k + D_k))
+    void *V;                 // three slots
+    I128 *part;              // [n][grid][3] per-CTA partial sums
+    double *alpha, *beta;    // [n][maxit1]
+    double *theta, *res;     // [n]
+    int *iters, *conv;       // [n]
+    double *tri_ws;          // [n][6 maxit1]
+    GridSync *gs;
+    unsigned long long limit_ns;
+    int withhold;            // CTA that leaves before its first arrival (the wait self-test), -1: none
+};
+
+// Store hook of the H·v (fixed point): w = H v - beta_prev vprev and the exact
+// sums <w, v>, <w, w>, <v, v> of the elements this thread wrote.
+struct FxStepEpi {
+    int64_t *w;
+    const int64_t *vprev;
+    int64_t Kb;
+    int Gb, has_prev;
+    I128 swv, sww, svv;
+    __device__ __forceinline__ void store(uint64_t i, int64_t hv, int64_t v) {
+        int64_t wi = hv;
+        if (has_prev) wi -= fx_mul(vprev[i], Kb, Gb);
+        w[i] = wi;
+        i128_add_prod(swv, wi, v);
+        i128_add_prod(sww, wi, wi);
+        i128_add_prod(svv, v, v);
+    }
+};
+
+// float64: w = H v - beta_prev vprev and <w, v> (the textbook first reduction)
+struct F64StepEpi {
+    double *w;
+    const double *vprev;
+    double bprev;
+    int has_prev;
+    double swv;
+    __device__ __forceinline__ void store(uint64_t i, double hv, double v) {
+        double wi = hv;
+        if (has_prev) wi = wi - bprev * vprev[i];
+        w[i] = wi;
+        swv = fma(wi, v, swv);
+    }
+};
+
+constexpr int kPThreads = 256;
+
+// first instance whose vector ends after element e (instances ordered by offset)
+__device__ __forceinline__ int inst_at(const Inst *inst, int n, uint64_t e) {
+    int lo = 0, hi = n - 1;  // largest k with off_k <= e
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].off <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Lanczos steps j = *jdev .. for every active instance, until chunk steps, maxit
+// or convergence of all.  Per step (fixed point): phase A, the H·v of all row
+// groups of all active instances fused with w = H v - beta vprev and the exact
+// sums (per-CTA partials per instance); barrier; phase C, alpha and beta of
+// every instance from the partials (double-double), w = (w - alpha v) / beta
+// over a contiguous slice of the batch vector per CTA, and, every check_every
+// steps, the tridiagonal solve of each instance by the CTA that holds its first
+// element; barrier.  float64 vectors take the textbook second reduction
+// (||w - alpha v||) in a phase B of its own.
+template <int R, int NC, bool FX>
+__global__ void __launch_bounds__(kPThreads, 3) k_batch_lanczos(PState p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];  // filled by copy_inst, no constructor
+    Inst &s_inst = *reinterpret_cast<Inst *>(s_inst_raw);
+    __shared__ int s_k;
+    __shared__ double s_ab[2];
+    using T = typename std::conditional<FX, int64_t, double>::type;
+    const unsigned G = gridDim.x;
+    const uint64_t n_items = p.prefix[p.n];
+    T *V = static_cast<T *>(p.V);
+    // this CTA's slice of the batch vector (phases B and C)
+    const uint64_t per = ((p.total + G - 1) / G + 3) & ~3ull;
+    const uint64_t c0 = min(p.total, (uint64_t)blockIdx.x * per), c1 = min(p.total, c0 + per);
+    int j = *p.jdev;
+    const int j_end = min(j + p.chunk, p.maxit);
+    unsigned tag = 0;
+    if ((int)blockIdx.x == p.withhold) return;  // self-test: this CTA never arrives
+    for (; j < j_end; ++j) {
+        int na = 0;
+        for (int k = 0; k < p.n; ++k) na += p.active[k];
+        if (na == 0) break;  // every CTA reads the same flags (set before the last barrier)
+        const int iv = j % 3, ip = (j + 2) % 3, iw = (j + 1) % 3;
+        // ---------------- phase A: H·v + first vector pass ----------------
+        for (int k = threadIdx.x; k < p.n; k += blockDim.x)
+            for (int q = 0; q < 3; ++q) p.part[((uint64_t)k * G + blockIdx.x) * 3 + q] = I128();
+        typename std::conditional<FX, FxStepEpi, F64StepEpi>::type epi{};
+        int cur = -1;
+        auto flush = [&](int k) {
+            if constexpr (FX) {
+                const I128 a = block_sum128(epi.swv), b = block_sum128(epi.sww), c = block_sum128(epi.svv);
+                if (threadIdx.x == 0) {
+                    I128 *dst = p.part + ((uint64_t)k * G + blockIdx.x) * 3;
+                    dst[0] = a, dst[1] = b, dst[2] = c;
+                }
+                epi.swv = epi.sww = epi.svv = I128();
+            } else {
+                const double a = block_sum_d(epi.swv);
+                if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3)[0] = a;
+                epi.swv = 0.0;
+            }
+        };
+        for (uint64_t it = blockIdx.x; it < n_items; it += G) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_k = find_inst(p.prefix, p.n, it);
+            __syncthreads();
+            const int k = s_k;
+            if (!p.active[k]) continue;  // uniform across the CTA
+            if (k != cur) {
+                if (cur >= 0) flush(cur);
+                __syncthreads();
+                copy_inst(&s_inst, p.inst + k);
+                __syncthreads();
+                if (FX) hv_fx_load_diag(s_inst.fx, smem);
+                cur = k;
+                const uint64_t off = s_inst.off;
+                epi.w = V + iw * p.stride + off;
+                epi.vprev = V + ip * p.stride + off;
+                epi.has_prev = j > 0;
+                const double bp = j > 0 ? p.beta[(uint64_t)k * p.maxit1 + j - 1] : 0.0;
+                if constexpr (FX) {
+                    const FxCoef c = fx_coef_dev(bp);
+                    epi.Kb = c.K;
+                    epi.Gb = c.G;
+                } else {
+                    epi.bprev = bp;
+                }
+            }
+            const uint64_t g = it - p.prefix[k];
+            const T *v = V + iv * p.stride + s_inst.off;
+            if constexpr (FX)
+                hv_fx_group<R, NC, true, true, FxStepEpi>(s_inst.fx, v, nullptr, g, smem, &epi);
+            else
+                hv_group<R, double, true, true, F64StepEpi>(s_inst.f64, v, nullptr, g, smem, &epi);
+        }
+        if (cur >= 0) flush(cur);
+        if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
+        // ---------------- phase B (float64 only): alpha, w -= alpha v, ||w||^2 ----------------
+        if constexpr (!FX) {
+            for (int k = threadIdx.x; k < p.n; k += blockDim.x)
+                reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3)[2] = 0.0;
+            if (c0 < c1) {
+                for (int k = inst_at(p.inst, p.n, c0); k < p.n && p.inst[k].off < c1; ++k) {
+                    if (!p.active[k]) continue;
+                    const Inst &in = p.inst[k];
+                    double s = 0.0;
+                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x)
+                        s += reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3)[0];
+                    s = block_sum_d(s);
+                    if (threadIdx.x == 0) s_ab[0] = s;
+                    __syncthreads();
+                    const double al = s_ab[0];
+                    const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
+                    double *w = V + iw * p.stride, *v = V + iv * p.stride;
+                    double acc = 0.0;
+                    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+                        const double wi = w[e] - al * v[e];
+                        w[e] = wi;
+                        acc = fma(wi, wi, acc);
+                    }
+                    acc = block_sum_d(acc);
+                    if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3)[2] = acc;
+                    __syncthreads();
+                }
+            }
+            if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
+        }
+        // ---------------- phase C: alpha, beta; w = (w - alpha v) / beta; checks ----------------
+        const bool check = (j + 1) % p.check_every == 0;
+        if (c0 < c1) {
+            for (int k = inst_at(p.inst, p.n, c0); k < p.n && p.inst[k].off < c1; ++k) {
+                if (!p.active[k]) continue;
+                const Inst &in = p.inst[k];
+                if constexpr (FX) {
+                    I128 t[3];
+                    for (int q = 0; q < 3; ++q) {
+                        I128 s;
+                        for (unsigned b = threadIdx.x; b < G; b += blockDim.x)
+                            i128_add(s, p.part[((uint64_t)k * G + b) * 3 + q]);
+                        t[q] = block_sum128(s);
+                    }
+                    if (threadIdx.x == 0) pdx::fx_alpha_beta(t, in.F, &s_ab[0], &s_ab[1]);
+                } else {
+                    double sa = 0.0, sb = 0.0;
+                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
+                        const double *q = reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3);
+                        sa += q[0];
+                        sb += q[2];
+                    }
+                    sa = block_sum_d(sa);
+                    sb = block_sum_d(sb);
+                    if (threadIdx.x == 0) {
+                        s_ab[0] = sa;
+                        s_ab[1] = sqrt(sb);
+                    }
+                }
+                __syncthreads();
+                const double al = s_ab[0], be = s_ab[1];
+                const bool owner = in.off >= c0;  // this CTA holds the instance's first element
+                if (owner && threadIdx.x == 0) {
+                    p.alpha[(uint64_t)k * p.maxit1 + j] = al;
+                    p.beta[(uint64_t)k * p.maxit1 + j] = be;
+                }
+                const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
+                T *w = V + iw * p.stride;
+                const T *v = V + iv * p.stride;
+                if constexpr (FX) {
+                    const FxCoef ca = fx_coef_dev(al), cf = fx_coef_dev(be != 0.0 ? 1.0 / be : 0.0);
+                    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+                        w[e] = fx_mul(w[e] - fx_mul(v[e], ca.K, ca.G), cf.K, cf.G);
+                } else {
+                    const double f = be != 0.0 ? 1.0 / be : 0.0;
+                    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) w[e] *= f;
+                }
+                const bool last = j + 1 >= p.maxit;
+                if (owner && (check || be == 0.0 || (uint64_t)(j + 1) >= in.D || last)) {
+                    __threadfence_block();
+                    __syncthreads();
+                    if (threadIdx.x < 32) {
+                        double th = 0.0, sl = 0.0;
+                        const int nn = j + 1;
+                        tri_lowest_warp(p.alpha + (uint64_t)k * p.maxit1, p.beta + (uint64_t)k * p.maxit1, nn,
+                                        p.tri_ws + (uint64_t)k * 6 * p.maxit1, &th, &sl);
+                        if (threadIdx.x == 0) {
+                            const double r = be * fabs(sl);
+                            p.theta[k] = th;
+                            p.res[k] = r;
+                            p.iters[k] = nn;
+                            const bool done = (p.tol > 0 && r <= p.tol * fmax(1.0, fabs(th))) || be == 0.0 ||
+                                              (uint64_t)nn >= in.D;
+                            if (done) {
+                                p.conv[k] = 1;
+                                p.active[k] = 0;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int na = 0;
+        for (int k = 0; k < p.n; ++k) na += p.active[k];
+        *p.jdev = j;
+        *p.n_active = na;
+    }
+}
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 }  // namespace
 
@@ -607,181 +872,223 @@ hb_status hubbard_batch_autotune(hb_batch_handle b, hb_dtype dt, const void *x, 
     return HB_OK;
 }
 
-static void batch_layout_ws(hb_batch_handle b, const hb_lanczos_opts *o, uint64_t *vec, uint64_t *part,
-                            uint64_t *ab, uint64_t *misc, uint64_t *total, int *nb) {
-    *nb = std::max(1, std::min(b->sm_count * 2, (int)((b->off[1] + 1023) / 1024)));
-    for (int k = 0; k < b->n; ++k) *nb = std::max(*nb, std::min(b->sm_count * 2, (int)((b->h[k]->D + 4095) / 4096)));
-    *vec = 0;
-    const uint64_t vbytes = align256(b->total * 8);
-    *part = *vec + 3 * vbytes;
-    *ab = *part + align256((uint64_t)b->n * (*nb) * 16);
-    *misc = *ab + align256((uint64_t)b->n * (o->maxit + 1) * 8 * 2);
-    *total = *misc + align256(sizeof(int) * (b->n + 1));
+}  // extern "C"
+
+namespace {
+
+// ---------------- batched Lanczos (host) ----------------
+struct BatchWs {
+    uint64_t vec, part_start, part, ab, tri, dbl, ints, sync, total;
+    int nb, gmax;
+};
+
+static BatchWs batch_layout_ws(hb_batch_handle b, const hb_lanczos_opts *o) {
+    BatchWs L;
+    L.nb = std::max(1, std::min(b->sm_count * 2, (int)((b->off[1] + 1023) / 1024)));
+    for (int k = 0; k < b->n; ++k) L.nb = std::max(L.nb, std::min(b->sm_count * 2, (int)((b->h[k]->D + 4095) / 4096)));
+    L.gmax = b->sm_count * (2048 / kPThreads);  // co-resident CTAs of the persistent kernel, at most
+    const uint64_t n = (uint64_t)b->n, m1 = (uint64_t)o->maxit + 1;
+    L.vec = 0;
+    L.part_start = L.vec + 3 * align256(b->total * 8);
+    L.part = L.part_start + align256(n * L.nb * 16);
+    L.ab = L.part + align256(n * L.gmax * 3 * 16);
+    L.tri = L.ab + align256(n * m1 * 8 * 2);
+    L.dbl = L.tri + align256(n * 6 * m1 * 8);
+    L.ints = L.dbl + align256(n * 2 * 8);
+    L.sync = L.ints + align256((3 * n + 2) * 4);
+    L.total = L.sync + 256;
+    return L;
 }
 
-hb_status lanczos_batch_workspace_bytes(hb_batch_handle b, const hb_lanczos_opts *o, uint64_t *bytes) {
-    if (!b || !o || !bytes || o->maxit < 1) return HB_ERR_INVALID_ARG;
-    uint64_t v, p, a, m;
-    int nb;
-    batch_layout_ws(b, o, &v, &p, &a, &m, bytes, &nb);
+template <int R, int NC, bool FX>
+hb_status pick_persistent(hb_batch *b, size_t smem, void **kern, int *per_sm) {
+    auto k = k_batch_lanczos<R, NC, FX>;
+    PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kPThreads, smem));
+    *kern = reinterpret_cast<void *>(k);
     return HB_OK;
 }
 
-// Batched three-term Lanczos (float64 or fixed-point vectors).  One step of
-// all active instances is 8 launches that take the step index from device
-// memory; `check_every` steps are captured once into a CUDA graph and the
-// graph is replayed between host-side convergence checks (per-instance
-// tridiagonal solves).  Converged instances are masked out of later steps.
-hb_status lanczos_batch_ground_state(hb_batch_handle b, const hb_lanczos_opts *o, void *workspace,
-                                     uint64_t workspace_bytes, double *E0, hb_lanczos_info *info, void *stream) {
+template <int R>
+hb_status pick_persistent_r(hb_batch *b, bool fx, size_t smem, void **kern, int *per_sm) {
+    if (!fx) return pick_persistent<R, 1, false>(b, smem, kern, per_sm);
+    switch (b->max_classes) {
+        case 1: return pick_persistent<R, 1, true>(b, smem, kern, per_sm);
+        case 2: return pick_persistent<R, 2, true>(b, smem, kern, per_sm);
+        case 3: return pick_persistent<R, 3, true>(b, smem, kern, per_sm);
+        default: return pick_persistent<R, 4, true>(b, smem, kern, per_sm);
+    }
+}
+
+// One cooperative launch of the persistent kernel (all CTAs co-resident, as its grid barriers need).
+hb_status launch_persistent(void *kern, unsigned grid, size_t smem, const PState &p, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kPThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {const_cast<PState *>(&p)};
+    PD_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
+    return HB_OK;
+}
+
+// The batched solve.  withhold >= 0 runs one step with that CTA leaving before
+// its first arrival and the given wait limit (the bounded-wait self-test).
+hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, uint64_t workspace_bytes,
+                        double *E0, hb_lanczos_info *info, cudaStream_t user, int withhold,
+                        unsigned long long limit_ns) {
     const auto t0 = std::chrono::steady_clock::now();
-    if (!b || !o || !workspace || !E0 || o->maxit < 1 || o->check_every < 1 || o->reorth) return HB_ERR_INVALID_ARG;
+    if (!b || !o || !workspace || o->maxit < 1 || o->check_every < 1 || o->reorth) return HB_ERR_INVALID_ARG;
     if (o->vec_dtype != HB_F64 && o->vec_dtype != HB_FX64) return HB_ERR_INVALID_ARG;
     const bool FX = o->vec_dtype == HB_FX64;
     if (FX)
         for (hb_handle h : b->h)
             if (!h->fx_ok) return HB_ERR_INVALID_ARG;
-    uint64_t ov, op, oab, om, total;
-    int nb;
-    batch_layout_ws(b, o, &ov, &op, &oab, &om, &total, &nb);
-    if (workspace_bytes < total) return HB_ERR_NO_MEMORY;
+    const BatchWs L = batch_layout_ws(b, o);
+    if (workspace_bytes < L.total) return HB_ERR_NO_MEMORY;
+    int coop = 0;
+    PD_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device));
+    if (!coop) return HB_ERR_CUDA;
+    const int R = b->rows == 1 ? 1 : 2;  // rows per item of the persistent kernel (fixed point stages at most 2)
     hb_status st = batch_prepare(b);
+    if (st == HB_OK && R != b->rows) st = build_desc(b, R);  // items of R rows (batch_prepare rebuilds for apply)
     if (st != HB_OK) return st;
+    const hb_dtype dt = FX ? HB_FX64 : HB_F64;
+    const size_t smem = batch_smem(b, R, dt);
+    void *kern = nullptr;
+    int per_sm = 0;
+    st = R == 1 ? pick_persistent_r<1>(b, FX, smem, &kern, &per_sm) : pick_persistent_r<2>(b, FX, smem, &kern, &per_sm);
+    if (st != HB_OK) return st;
+    if (per_sm < 1) return HB_ERR_NO_MEMORY;
+    const unsigned grid = (unsigned)std::min(per_sm * b->sm_count, L.gmax);
+
     char *ws = static_cast<char *>(workspace);
     const int n = b->n, maxit1 = o->maxit + 1;
-    BState S;
-    S.inst = b->d_inst;
-    S.stride = align256(b->total * 8) / 8;
-    S.n = n;
-    S.maxit1 = maxit1;
-    S.nb = nb;
-    S.V = ws + ov;
-    S.part = reinterpret_cast<I128 *>(ws + op);
-    S.alpha = reinterpret_cast<double *>(ws + oab);
-    S.beta = S.alpha + (uint64_t)n * maxit1;
-    int *d_active = reinterpret_cast<int *>(ws + om);
-    int *d_j = d_active + n;
-    S.active = d_active;
-    S.j = d_j;
+    PState p;
+    p.inst = b->d_inst;
+    p.prefix = b->d_prefix;
+    p.n = n;
+    p.maxit = withhold >= 0 ? 1 : o->maxit;
+    p.maxit1 = maxit1;
+    p.check_every = o->check_every;
+    p.tol = o->tol;
+    p.chunk = withhold >= 0 ? 1 : std::min(o->maxit, 64);
+    p.stride = align256(b->total * 8) / 8;
+    p.total = b->total;
+    p.V = ws + L.vec;
+    p.part = reinterpret_cast<I128 *>(ws + L.part);
+    p.alpha = reinterpret_cast<double *>(ws + L.ab);
+    p.beta = p.alpha + (uint64_t)n * maxit1;
+    p.tri_ws = reinterpret_cast<double *>(ws + L.tri);
+    p.theta = reinterpret_cast<double *>(ws + L.dbl);
+    p.res = p.theta + n;
+    p.active = reinterpret_cast<int *>(ws + L.ints);
+    p.iters = p.active + n;
+    p.conv = p.iters + n;
+    p.jdev = p.conv + n;
+    p.n_active = p.jdev + 1;
+    p.gs = reinterpret_cast<GridSync *>(ws + L.sync);
+    p.limit_ns = limit_ns;
+    p.withhold = withhold;
 
-    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
     cudaStream_t cs;
     PD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaEvent_t ev;
-    PD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return HB_ERR_CUDA;
+    }
     cudaEventRecord(ev, user);
     cudaStreamWaitEvent(cs, ev, 0);  // ordered after the caller's earlier work
-    std::vector<int> act(n, 1);
-    cudaMemcpyAsync(d_active, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, cs);
-    cudaMemsetAsync(d_j, 0, sizeof(int), cs);
-    const dim3 gv(nb, n);
-    // start vectors in slot 0, normalised
+    std::vector<int> ones(n, 1);
+    cudaMemcpyAsync(p.active, ones.data(), sizeof(int) * n, cudaMemcpyHostToDevice, cs);
+    cudaMemsetAsync(p.iters, 0, sizeof(int) * (2 * n + 2), cs);  // iters, conv, jdev, n_active
+    cudaMemsetAsync(p.gs, 0, sizeof(GridSync), cs);
+    cudaMemsetAsync(p.alpha, 0, sizeof(double) * 2 * (uint64_t)n * maxit1, cs);
+    StartState ss{b->d_inst, p.V, reinterpret_cast<I128 *>(ws + L.part_start), L.nb};
+    const dim3 gv(L.nb, n);
     if (FX) {
-        k_b_fill<true><<<gv, kThreads, 0, cs>>>(S, o->seed);
-        // norms of un-normalised vectors: products shifted as in the single-instance path
-        k_b_norm_partials<true><<<gv, kThreads, 0, cs>>>(S);
-        k_b_normalise<true><<<n, kFinal, 0, cs>>>(S);
+        k_b_fill<true><<<gv, kThreads, 0, cs>>>(ss, o->seed);
+        k_b_norm_partials<true><<<gv, kThreads, 0, cs>>>(ss);
+        k_b_normalise<true><<<n, kFinal, 0, cs>>>(ss);
     } else {
-        k_b_fill<false><<<gv, kThreads, 0, cs>>>(S, o->seed);
-        k_b_norm_partials<false><<<gv, kThreads, 0, cs>>>(S);
-        k_b_normalise<false><<<n, kFinal, 0, cs>>>(S);
+        k_b_fill<false><<<gv, kThreads, 0, cs>>>(ss, o->seed);
+        k_b_norm_partials<false><<<gv, kThreads, 0, cs>>>(ss);
+        k_b_normalise<false><<<n, kFinal, 0, cs>>>(ss);
     }
-    PD_CUDA(cudaGetLastError());
-    const hb_dtype dt = FX ? HB_FX64 : HB_F64;
-    // One graph per slot phase p = j mod 3 (the batched H·v takes its vector pointers as
-    // launch arguments, the vector kernels read j from device memory); each graph holds one
-    // step, and steps are replayed phase after phase.
-    if ((st = batch_hv(b, dt, S.V, static_cast<char *>(S.V) + S.stride * 8, d_active, cs)) != HB_OK) return st;
-    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
-    hb_status cap = HB_OK;
-    for (int p = 0; p < 3 && cap == HB_OK; ++p) {
-        const uint64_t es = 8;
-        char *Vb = static_cast<char *>(S.V);
-        const void *v = Vb + (uint64_t)(p % 3) * S.stride * es;
-        void *w = Vb + (uint64_t)((p + 1) % 3) * S.stride * es;
-        cudaGraph_t g;
-        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-            cap = HB_ERR_CUDA;
-            break;
+    hb_status run = cudaGetLastError() == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+
+    // one chunk of steps = one cooperative launch, captured once into a graph and replayed
+    cudaGraphExec_t exec = nullptr;
+    if (run == HB_OK && withhold < 0) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) run = HB_ERR_CUDA;
+        if (run == HB_OK) {
+            const hb_status ls = launch_persistent(kern, grid, smem, p, cs);
+            const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+            if (ls != HB_OK || ce != cudaSuccess) run = HB_ERR_CUDA;
         }
-        hb_status s1 = batch_hv(b, dt, v, w, d_active, cs);
-        if (FX) {
-            k_b_axpy_dot<true><<<gv, kThreads, 0, cs>>>(S);
-            k_b_reduce<true><<<n, kFinal, 0, cs>>>(S, 0);
-            k_b_axpy_norm<true><<<gv, kThreads, 0, cs>>>(S);
-            k_b_reduce<true><<<n, kFinal, 0, cs>>>(S, 1);
-            k_b_scale<true><<<gv, kThreads, 0, cs>>>(S);
-        } else {
-            k_b_axpy_dot<false><<<gv, kThreads, 0, cs>>>(S);
-            k_b_reduce<false><<<n, kFinal, 0, cs>>>(S, 0);
-            k_b_axpy_norm<false><<<gv, kThreads, 0, cs>>>(S);
-            k_b_reduce<false><<<n, kFinal, 0, cs>>>(S, 1);
-            k_b_scale<false><<<gv, kThreads, 0, cs>>>(S);
-        }
-        k_b_advance<<<1, 1, 0, cs>>>(d_j);
-        cudaError_t ce = cudaStreamEndCapture(cs, &g);
-        if (s1 != HB_OK || ce != cudaSuccess) {
-            cap = s1 != HB_OK ? s1 : HB_ERR_CUDA;
-            break;
-        }
-        if (cudaGraphInstantiate(&exec[p], g, 0) != cudaSuccess) cap = HB_ERR_CUDA;
-        cudaGraphDestroy(g);
+        if (run == HB_OK && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) run = HB_ERR_CUDA;
+        if (g) cudaGraphDestroy(g);
     }
-    std::vector<double> ha((size_t)n * maxit1), hbv((size_t)n * maxit1);
-    std::vector<int> iters(n, 0), conv(n, 0);
-    std::vector<double> theta(n, NAN), res(n, INFINITY);
-    int j = 0, n_active = n;
-    while (cap == HB_OK && j < o->maxit && n_active > 0) {
-        const int chunk = std::min(o->check_every, o->maxit - j);
-        for (int c = 0; c < chunk; ++c, ++j)
-            if (cudaGraphLaunch(exec[j % 3], cs) != cudaSuccess) {
-                cap = HB_ERR_CUDA;
-                break;
-            }
-        if (cap != HB_OK) break;
-        cudaMemcpyAsync(ha.data(), S.alpha, sizeof(double) * n * maxit1, cudaMemcpyDeviceToHost, cs);
-        cudaMemcpyAsync(hbv.data(), S.beta, sizeof(double) * n * maxit1, cudaMemcpyDeviceToHost, cs);
+    struct {
+        int j, n_active;
+        GridSync gs;
+    } hs = {};
+    while (run == HB_OK) {
+        if (withhold >= 0)
+            run = launch_persistent(kern, grid, smem, p, cs);
+        else if (cudaGraphLaunch(exec, cs) != cudaSuccess)
+            run = HB_ERR_CUDA;
+        if (run != HB_OK) break;
+        cudaMemcpyAsync(&hs.j, p.jdev, sizeof(int) * 2, cudaMemcpyDeviceToHost, cs);
+        cudaMemcpyAsync(&hs.gs, p.gs, sizeof(GridSync), cudaMemcpyDeviceToHost, cs);
         if (cudaStreamSynchronize(cs) != cudaSuccess) {
-            cap = HB_ERR_CUDA;
+            run = HB_ERR_CUDA;
             break;
         }
-        bool changed = false;
-        for (int k = 0; k < n; ++k) {
-            if (!act[k]) continue;
-            const double *a = ha.data() + (size_t)k * maxit1;
-            const double *bb = hbv.data() + (size_t)k * maxit1;
-            double th, sl;
-            tridiag_lowest(a, bb, j, &th, &sl);
-            theta[k] = th;
-            res[k] = bb[j - 1] * std::fabs(sl);
-            iters[k] = j;
-            const bool exhausted = bb[j - 1] == 0.0 || (uint64_t)j >= b->h[k]->D;
-            if ((o->tol > 0 && res[k] <= o->tol * std::max(1.0, std::fabs(th))) || exhausted) {
-                conv[k] = 1;
-                act[k] = 0;
-                --n_active;
-                changed = true;
-            }
+        if (hs.gs.abort) {
+            run = HB_ERR_TIMEOUT;
+            break;
         }
-        if (changed) cudaMemcpyAsync(d_active, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, cs);
+        if (hs.n_active == 0 || hs.j >= p.maxit) break;
     }
     cudaStreamSynchronize(cs);
-    for (auto &e : exec)
-        if (e) cudaGraphExecDestroy(e);
+    if (exec) cudaGraphExecDestroy(exec);
+    std::vector<double> ha((size_t)n * maxit1), hbv((size_t)n * maxit1);
+    std::vector<int> iters(n), conv(n);
+    if (run == HB_OK) {
+        cudaMemcpyAsync(ha.data(), p.alpha, sizeof(double) * n * maxit1, cudaMemcpyDeviceToHost, cs);
+        cudaMemcpyAsync(hbv.data(), p.beta, sizeof(double) * n * maxit1, cudaMemcpyDeviceToHost, cs);
+        cudaMemcpyAsync(iters.data(), p.iters, sizeof(int) * n, cudaMemcpyDeviceToHost, cs);
+        cudaMemcpyAsync(conv.data(), p.conv, sizeof(int) * n, cudaMemcpyDeviceToHost, cs);
+        if (cudaStreamSynchronize(cs) != cudaSuccess) run = HB_ERR_CUDA;
+    }
     cudaEventRecord(ev, cs);
     cudaStreamWaitEvent(user, ev, 0);
     cudaEventDestroy(ev);
     cudaStreamDestroy(cs);
-    if (cap != HB_OK) return cap;
+    if (run != HB_OK) return run;
+    // final values on the host from the recorded coefficients (the same solver as every other Lanczos call)
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     bool all = true;
     for (int k = 0; k < n; ++k) {
-        E0[k] = theta[k];
+        const int nn = std::max(1, iters[k]);
+        const double *a = ha.data() + (size_t)k * maxit1;
+        const double *bb = hbv.data() + (size_t)k * maxit1;
+        double th = NAN, sl = 0.0;
+        hb_tridiag_lowest(a, bb, nn, &th, &sl);
+        if (E0) E0[k] = th;
         all = all && conv[k];
         if (info) {
-            info[k].E0 = theta[k];
-            info[k].residual = res[k];
-            info[k].iterations = iters[k];
+            info[k].E0 = th;
+            info[k].residual = bb[nn - 1] * std::fabs(sl);
+            info[k].iterations = nn;
             info[k].iterations_f32 = 0;
             info[k].status = conv[k] || o->tol <= 0 ? HB_OK : HB_ERR_NOT_CONVERGED;
             info[k].converged = conv[k];
@@ -789,6 +1096,31 @@ hb_status lanczos_batch_ground_state(hb_batch_handle b, const hb_lanczos_opts *o
         }
     }
     return all || o->tol <= 0 ? HB_OK : HB_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+hb_status lanczos_batch_workspace_bytes(hb_batch_handle b, const hb_lanczos_opts *o, uint64_t *bytes) {
+    if (!b || !o || !bytes || o->maxit < 1) return HB_ERR_INVALID_ARG;
+    *bytes = batch_layout_ws(b, o).total;
+    return HB_OK;
+}
+
+hb_status lanczos_batch_ground_state(hb_batch_handle b, const hb_lanczos_opts *o, void *workspace,
+                                     uint64_t workspace_bytes, double *E0, hb_lanczos_info *info, void *stream) {
+    if (!E0) return HB_ERR_INVALID_ARG;
+    return batch_lanczos(b, o, workspace, workspace_bytes, E0, info, reinterpret_cast<cudaStream_t>(stream), -1,
+                         5000000000ull);
+}
+
+hb_status lanczos_batch_wait_selftest(hb_batch_handle b, const hb_lanczos_opts *o, void *workspace,
+                                      uint64_t workspace_bytes, int32_t withhold_cta, uint32_t limit_ms,
+                                      void *stream) {
+    if (withhold_cta < 0 || limit_ms < 1 || limit_ms > 10000) return HB_ERR_INVALID_ARG;
+    return batch_lanczos(b, o, workspace, workspace_bytes, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream),
+                         withhold_cta, (unsigned long long)limit_ms * 1000000ull);
 }
 
 }  // extern "C"

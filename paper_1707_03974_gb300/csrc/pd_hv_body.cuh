@@ -69,9 +69,11 @@ __host__ __device__ inline size_t hv_smem_bytes(int R, int zmax, size_t tsize, u
 // diagonal and spin-down terms are summed first and the spin-up terms in a
 // separate accumulator, y = (diag + down) + up, so that the split form (this
 // body with DO_A = false followed by hv_up_item) gives bit-identical results.
-template <int R, typename T, bool SMEM, bool DO_A = true>
+// Epi: optional store hook (the batched Lanczos step fuses its first vector pass
+// here); with the default (void) every output is stored to y.
+template <int R, typename T, bool SMEM, bool DO_A = true, class Epi = void>
 __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict__ x, T *__restrict__ y, uint64_t g,
-                                         unsigned char *smem) {
+                                         unsigned char *smem, Epi *epi = nullptr) {
     const uint64_t Dd = a.Dd;
     uint64_t *s_uoff = reinterpret_cast<uint64_t *>(smem);  // spin-up hop rows as element offsets u' * D_dn
     const int zr = a.zmax_up > 0 ? a.zmax_up : 1;
@@ -155,7 +157,14 @@ __device__ __forceinline__ void hv_group(const HvArgs<T> &a, const T *__restrict
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (r < nr) y[ur[r] * Dd + d] = acc[r];
+            if (r < nr) {
+                if constexpr (std::is_void<Epi>::value) {
+                    y[ur[r] * Dd + d] = acc[r];
+                } else {
+                    const T xv = SMEM ? s_x[d * R + r] : x[ur[r] * Dd + d];
+                    epi->store(ur[r] * Dd + d, acc[r], xv);
+                }
+            }
     }
 }
 
@@ -207,9 +216,9 @@ __device__ __forceinline__ void hv_fx_load_diag(const FxArgs &a, unsigned char *
     }
 }
 
-template <int R, int NC, bool SMEM, bool DO_A = true>
+template <int R, int NC, bool SMEM, bool DO_A = true, class Epi = void>
 __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__restrict__ x, int64_t *__restrict__ y,
-                                            uint64_t g, unsigned char *smem) {
+                                            uint64_t g, unsigned char *smem, Epi *epi = nullptr) {
     const uint64_t Dd = a.Dd;
     const int zr = a.zmax_up > 0 ? a.zmax_up : 1;
     const int64_t *s_kd = reinterpret_cast<const int64_t *>(smem);
@@ -310,7 +319,12 @@ __device__ __forceinline__ void hv_fx_group(const FxArgs &a, const int64_t *__re
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (r >= nr) continue;
-            y[ur[r] * Dd + d] = out[r];
+            if constexpr (std::is_void<Epi>::value) {
+                y[ur[r] * Dd + d] = out[r];
+            } else {
+                const int64_t xd = SMEM ? s_x[d * R + r] : x[ur[r] * Dd + d];
+                epi->store(ur[r] * Dd + d, out[r], xd);
+            }
         }
     }
 }

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "pd_common.cuh"
+#include "pd_exact.cuh"
 
 namespace {
 
@@ -302,60 +303,13 @@ __global__ void k_copy(const T *__restrict__ a, T *__restrict__ b, uint64_t n) {
 }
 
 // ---------------- fixed-point (HB_FX64) vector kernels ----------------
-// Dot products of fixed-point vectors are exact: each 64x64-bit product is
-// kept as a 128-bit integer and summed in 128 bits (per thread, per block and
-// across blocks, in a fixed order), then converted to float64 once.
-struct I128 {
-    uint64_t lo = 0;
-    int64_t hi = 0;
-};
-
-__device__ __forceinline__ void i128_add_prod(I128 &s, int64_t a, int64_t b) {
-    const int64_t ph = __mul64hi(a, b);
-    const uint64_t pl = (uint64_t)a * (uint64_t)b;
-    const uint64_t lo = s.lo + pl;
-    s.hi += ph + (lo < pl ? 1 : 0);
-    s.lo = lo;
-}
-
-__device__ __forceinline__ void i128_add(I128 &s, const I128 &t) {
-    const uint64_t lo = s.lo + t.lo;
-    s.hi += t.hi + (lo < t.lo ? 1 : 0);
-    s.lo = lo;
-}
-
-__device__ __forceinline__ I128 block_sum128(I128 v) {
-    __shared__ uint64_t s_lo[32];
-    __shared__ int64_t s_hi[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        I128 t;
-        t.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
-        t.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
-        i128_add(v, t);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) {
-        s_lo[wid] = v.lo;
-        s_hi[wid] = v.hi;
-    }
-    __syncthreads();
-    I128 r;
-    if (wid == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        if (lane < nw) {
-            r.lo = s_lo[lane];
-            r.hi = s_hi[lane];
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            I128 t;
-            t.lo = __shfl_down_sync(0xffffffffu, r.lo, o);
-            t.hi = __shfl_down_sync(0xffffffffu, r.hi, o);
-            i128_add(r, t);
-        }
-    }
-    return r;  // valid in thread 0
-}
+// Dot products of fixed-point vectors are exact (pd_exact.cuh): 128-bit sums of
+// the 64 x 64-bit products, per thread, per block and across blocks in a fixed
+// order, converted to float64 once.
+using pdx::I128;
+using pdx::block_sum128;
+using pdx::i128_add;
+using pdx::i128_add_prod;
 
 __global__ void k_fx_scale(int64_t *__restrict__ v, const double *__restrict__ den, uint64_t n) {
     const double d = *den;
@@ -417,38 +371,6 @@ __global__ void k_fx_axpy_dot3(int64_t *__restrict__ w, const int64_t *__restric
     }
 }
 
-// double-double helpers (Dekker / Knuth error-free transformations)
-struct DD {
-    double h, l;
-};
-__device__ __forceinline__ DD dd_two_sum(double a, double b) {
-    const double s = a + b, bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ DD dd_norm(double s, double e) {
-    const double t = s + e;
-    return {t, e - (t - s)};
-}
-__device__ __forceinline__ DD dd_add(DD x, DD y) {
-    DD s = dd_two_sum(x.h, y.h);
-    return dd_norm(s.h, s.l + x.l + y.l);
-}
-__device__ __forceinline__ DD dd_mul_d(DD x, double y) {
-    const double p = x.h * y;
-    return dd_norm(p, fma(x.h, y, -p) + x.l * y);
-}
-// a 128-bit integer times 2^sh as a double-double: the four 32-bit pieces are exact doubles
-__device__ __forceinline__ DD dd_of_i128(I128 s, int sh) {
-    const double h1 = ldexp((double)(int32_t)(uint32_t)((uint64_t)s.hi >> 32), 96 + sh);
-    const double h0 = ldexp((double)(uint32_t)((uint64_t)s.hi & 0xFFFFFFFFu), 64 + sh);
-    const double l1 = ldexp((double)(uint32_t)(s.lo >> 32), 32 + sh);
-    const double l0 = ldexp((double)(uint32_t)(s.lo & 0xFFFFFFFFu), sh);
-    DD r = {h1, 0.0};
-    r = dd_add(r, {h0, 0.0});
-    r = dd_add(r, {l1, 0.0});
-    return dd_add(r, {l0, 0.0});
-}
-
 // alpha = <w, v>; beta = sqrt(<w,w> - 2 alpha <w,v> + alpha^2 <v,v>) with the
 // alpha that pass 2 applies (the float64 value written to *alpha)
 __global__ void k_fx_alpha_beta(const I128 *__restrict__ partials, int nb, double *__restrict__ alpha,
@@ -459,15 +381,7 @@ __global__ void k_fx_alpha_beta(const I128 *__restrict__ partials, int nb, doubl
         for (int i = threadIdx.x; i < nb; i += blockDim.x) i128_add(s, partials[k * nb + i]);
         t[k] = block_sum128(s);
     }
-    if (threadIdx.x == 0) {
-        const DD swv = dd_of_i128(t[0], -2 * F), sww = dd_of_i128(t[1], -2 * F), svv = dd_of_i128(t[2], -2 * F);
-        const double al = swv.h + swv.l;
-        DD b2 = dd_add(sww, dd_mul_d(swv, -2.0 * al));
-        b2 = dd_add(b2, dd_mul_d(dd_mul_d(svv, al), al));
-        const double v = b2.h + b2.l;
-        alpha[0] = al;
-        beta[0] = v > 0.0 ? sqrt(v) : 0.0;
-    }
+    if (threadIdx.x == 0) pdx::fx_alpha_beta(t, F, alpha, beta);
 }
 
 // w = (w - alpha v) / beta  (without the division when !scale)

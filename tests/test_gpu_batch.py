@@ -66,3 +66,44 @@ def test_batch_lanczos_matches_oracle(batch, dtype_name):
     for k in range(64):
         assert infos[k]["converged"]
         assert abs(E0[k] - g[k]["E0"]) <= 1e-10 * max(1.0, abs(g[k]["E0"])), (k, E0[k], g[k]["E0"])
+
+
+def test_batch_lanczos_uneven_subset_and_iteration_counts(batch):
+    """A batch of four very uneven instances (the smallest and largest of the draw, rings and 3x4):
+    every E0 within 1e-10 of the oracle, each instance stopping at its own iteration count."""
+    torch, pd, insts, hs, b = batch
+    g = gold()
+    D = [h.D for h in hs]
+    pick = sorted({int(np.argmin(D)), int(np.argmax(D)), 0, 63})
+    sub = pd.Batch([hs[k] for k in pick])
+    E0, infos, status = pd.lanczos_batch_ground_state(sub, maxit=1500, tol=1e-10, dtype=torch.int64, seed=0,
+                                                      check_every=7)
+    assert status == "HB_OK"
+    for i, k in enumerate(pick):
+        assert infos[i]["converged"]
+        assert infos[i]["iterations"] % 7 == 0 or infos[i]["iterations"] >= hs[k].D
+        assert abs(E0[i] - g[k]["E0"]) <= 1e-10 * max(1.0, abs(g[k]["E0"])), (k, E0[i], g[k]["E0"])
+    sub.close()
+
+
+def test_batch_lanczos_maxit_reports_not_converged(batch):
+    torch, pd, insts, hs, b = batch
+    E0, infos, status = pd.lanczos_batch_ground_state(b, maxit=5, tol=1e-10, dtype=torch.int64, seed=0,
+                                                      check_every=10)
+    assert status == "HB_ERR_NOT_CONVERGED"
+    assert all(i["iterations"] == 5 and not i["converged"] for i in infos)
+    g = gold()
+    assert all(e >= gk["E0"] - 1e-9 for e, gk in zip(E0, g))  # Ritz values bound E0 from above
+
+
+@pytest.mark.parametrize("withhold", [0, 5])
+def test_batch_grid_wait_gives_up(batch, withhold):
+    """A CTA that never arrives at the grid barrier: the other CTAs' waits give up after 50 ms and the
+    solve reports HB_ERR_TIMEOUT instead of hanging; the batch solves correctly right after."""
+    torch, pd, insts, hs, b = batch
+    assert pd.lanczos_batch_wait_selftest(b, withhold_cta=withhold, limit_ms=50) == "HB_ERR_TIMEOUT"
+    E0, infos, status = pd.lanczos_batch_ground_state(b, maxit=1500, tol=1e-10, dtype=torch.int64, seed=0,
+                                                      check_every=10)
+    assert status == "HB_OK"
+    g = gold()
+    assert max(abs(e - gk["E0"]) / max(1.0, abs(gk["E0"])) for e, gk in zip(E0, g)) <= 1e-10
