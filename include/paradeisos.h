@@ -218,6 +218,10 @@ typedef struct {
                              in binary64 vectors (1) or HB_FX64 vectors (2) */
     int32_t f32_tol_exp;  /* binary32 phase ends when the residual <= 10^f32_tol_exp * max(1,|theta|)
                              or stops improving (default -5 when 0) */
+    int32_t store_basis;  /* with vec_dtype HB_F32 and fp64_finish: K > 0 keeps the binary32 Krylov
+                             vectors v_0 .. v_K in the workspace (K + 1 vectors of 4 D bytes), caps the
+                             binary32 phase at K steps and forms its Ritz vector in one pass over them
+                             instead of replaying the recurrence; 0: replay (three vectors) */
 } hb_lanczos_opts;
 
 typedef struct {

@@ -45,7 +45,7 @@ class HvConfig(ctypes.Structure):
 class LanczosOpts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int32), ("reorth", ctypes.c_int32), ("vec_dtype", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("fp64_finish", ctypes.c_int32), ("f32_tol_exp", ctypes.c_int32)]
+                ("fp64_finish", ctypes.c_int32), ("f32_tol_exp", ctypes.c_int32), ("store_basis", ctypes.c_int32)]
 
 
 class LanczosInfo(ctypes.Structure):
@@ -384,13 +384,14 @@ class LanczosResult:
 
 def lanczos_ground_state(h: Handle, maxit: int = 300, tol: float = 1e-10, reorth: bool = False, dtype=None,
                          seed: int = 0, v0=None, check_every: int = 1, fp64_finish: bool = False,
-                         f32_tol_exp: int = 0, workspace=None, stream=None, raise_on_error: bool = True) -> LanczosResult:
+                         f32_tol_exp: int = 0, store_basis: int = 0, workspace=None, stream=None,
+                         raise_on_error: bool = True) -> LanczosResult:
     import torch
     dt = {None: HB_F64, torch.float64: HB_F64, torch.float32: HB_F32, torch.int64: HB_FX64}[dtype]
     fin = {False: 0, True: 1, "f64": 1, "fx64": 2}[fp64_finish] if not isinstance(fp64_finish, int) or \
         isinstance(fp64_finish, bool) else int(fp64_finish)
     o = LanczosOpts(int(maxit), int(bool(reorth)), dt, int(check_every), float(tol), int(seed) & ((1 << 64) - 1),
-                    fin, int(f32_tol_exp))
+                    fin, int(f32_tol_exp), int(store_basis))
     lib = load()
     nb = ctypes.c_uint64()
     _check(lib.lanczos_workspace_bytes(h.ptr, ctypes.byref(o), ctypes.byref(nb)), "lanczos_workspace_bytes")

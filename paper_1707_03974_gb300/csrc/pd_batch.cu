@@ -381,20 +381,18 @@ struct PState {
 };
 
 // Store hook of the H·v (fixed point): w = H v - beta_prev vprev and the exact
-// sums <w, v>, <w, w>, <v, v> of the elements this thread wrote.
+// sum <w, v> of the elements this thread wrote.
 struct FxStepEpi {
     int64_t *w;
     const int64_t *vprev;
     int64_t Kb;
     int Gb, has_prev;
-    I128 swv, sww, svv;
+    I128 swv;
     __device__ __forceinline__ void store(uint64_t i, int64_t hv, int64_t v) {
         int64_t wi = hv;
         if (has_prev) wi -= fx_mul(vprev[i], Kb, Gb);
         w[i] = wi;
         i128_add_prod(swv, wi, v);
-        i128_add_prod(sww, wi, wi);
-        i128_add_prod(svv, v, v);
     }
 };
 
@@ -414,6 +412,24 @@ struct F64StepEpi {
 };
 
 constexpr int kPThreads = 256;
+constexpr int kSmemPrefix = 512;  // batches of up to this many instances keep their item prefix sums in shared memory
+
+// f(e) for every element e of [e0, e1) handled by this thread: four elements
+// (e, e + T, e + 2T, e + 3T) per round so that each thread keeps several loads
+// in flight, then the remainder one by one.  f(e) must not depend on another
+// element's result.
+template <typename Fn>
+__device__ __forceinline__ void slice_x4(uint64_t e0, uint64_t e1, Fn f) {
+    const uint64_t T = blockDim.x;
+    uint64_t e = e0 + threadIdx.x;
+    for (; e + 3 * T < e1; e += 4 * T) {
+        f(e);
+        f(e + T);
+        f(e + 2 * T);
+        f(e + 3 * T);
+    }
+    for (; e < e1; e += T) f(e);
+}
 
 // first instance whose vector ends after element e (instances ordered by offset)
 __device__ __forceinline__ int inst_at(const Inst *inst, int n, uint64_t e) {
@@ -426,21 +442,27 @@ __device__ __forceinline__ int inst_at(const Inst *inst, int n, uint64_t e) {
 }
 
 // Lanczos steps j = *jdev .. for every active instance, until chunk steps, maxit
-// or convergence of all.  Per step (fixed point): phase A, the H·v of all row
-// groups of all active instances fused with w = H v - beta vprev and the exact
-// sums (per-CTA partials per instance); barrier; phase C, alpha and beta of
-// every instance from the partials (double-double), w = (w - alpha v) / beta
-// over a contiguous slice of the batch vector per CTA, and, every check_every
-// steps, the tridiagonal solve of each instance by the CTA that holds its first
-// element; barrier.  float64 vectors take the textbook second reduction
-// (||w - alpha v||) in a phase B of its own.
+// or convergence of all.  Per step: phase A, the H·v of all row groups of all
+// active instances fused with w = H v - beta vprev and the first reduction
+// <w, v> (per-CTA partials per instance); barrier; phase B, alpha = <w, v>,
+// w -= alpha v and the partials of ||w||^2 over a contiguous slice of the batch
+// vector per CTA; barrier; phase C, beta = ||w||, w /= beta, and, every
+// check_every steps, the tridiagonal solve of each instance by the CTA that
+// holds its first element; barrier.  With fixed-point vectors both reductions
+// are exact 128-bit sums (converted to float64 once, through double-double).
 template <int R, int NC, bool FX>
-__global__ void __launch_bounds__(kPThreads, 3) k_batch_lanczos(PState p) {
+__global__ void __launch_bounds__(kPThreads, (FX && NC <= 2) ? 4 : 3) k_batch_lanczos(PState p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];  // filled by copy_inst, no constructor
     Inst &s_inst = *reinterpret_cast<Inst *>(s_inst_raw);
     __shared__ int s_k;
     __shared__ double s_ab[2];
+    __shared__ uint64_t s_prefix[kSmemPrefix + 1];  // item prefix sums, when the batch is small enough
+    const bool pre_smem = p.n <= kSmemPrefix;
+    if (pre_smem)
+        for (int k = threadIdx.x; k <= p.n; k += blockDim.x) s_prefix[k] = p.prefix[k];
+    __syncthreads();
+    const uint64_t *prefix = pre_smem ? s_prefix : p.prefix;
     using T = typename std::conditional<FX, int64_t, double>::type;
     const unsigned G = gridDim.x;
     const uint64_t n_items = p.prefix[p.n];
@@ -464,12 +486,9 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_lanczos(PState p) {
         int cur = -1;
         auto flush = [&](int k) {
             if constexpr (FX) {
-                const I128 a = block_sum128(epi.swv), b = block_sum128(epi.sww), c = block_sum128(epi.svv);
-                if (threadIdx.x == 0) {
-                    I128 *dst = p.part + ((uint64_t)k * G + blockIdx.x) * 3;
-                    dst[0] = a, dst[1] = b, dst[2] = c;
-                }
-                epi.swv = epi.sww = epi.svv = I128();
+                const I128 a = block_sum128(epi.swv);
+                if (threadIdx.x == 0) p.part[((uint64_t)k * G + blockIdx.x) * 3] = a;
+                epi.swv = I128();
             } else {
                 const double a = block_sum_d(epi.swv);
                 if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3)[0] = a;
@@ -478,7 +497,7 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_lanczos(PState p) {
         };
         for (uint64_t it = blockIdx.x; it < n_items; it += G) {
             __syncthreads();
-            if (threadIdx.x == 0) s_k = find_inst(p.prefix, p.n, it);
+            if (threadIdx.x == 0) s_k = find_inst(prefix, p.n, it);
             __syncthreads();
             const int k = s_k;
             if (!p.active[k]) continue;  // uniform across the CTA
@@ -502,7 +521,7 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_lanczos(PState p) {
                     epi.bprev = bp;
                 }
             }
-            const uint64_t g = it - p.prefix[k];
+            const uint64_t g = it - prefix[k];
             const T *v = V + iv * p.stride + s_inst.off;
             if constexpr (FX)
                 hv_fx_group<R, NC, true, true, FxStepEpi>(s_inst.fx, v, nullptr, g, smem, &epi);
@@ -511,36 +530,53 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_lanczos(PState p) {
         }
         if (cur >= 0) flush(cur);
         if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
-        // ---------------- phase B (float64 only): alpha, w -= alpha v, ||w||^2 ----------------
-        if constexpr (!FX) {
-            for (int k = threadIdx.x; k < p.n; k += blockDim.x)
-                reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3)[2] = 0.0;
-            if (c0 < c1) {
-                for (int k = inst_at(p.inst, p.n, c0); k < p.n && p.inst[k].off < c1; ++k) {
-                    if (!p.active[k]) continue;
-                    const Inst &in = p.inst[k];
-                    double s = 0.0;
+        // ---------------- phase B: alpha = <w, v>; w -= alpha v; partial ||w||^2 ----------------
+        for (int k = threadIdx.x; k < p.n; k += blockDim.x) p.part[((uint64_t)k * G + blockIdx.x) * 3 + 1] = I128();
+        if (c0 < c1) {
+            for (int k = inst_at(p.inst, p.n, c0); k < p.n && p.inst[k].off < c1; ++k) {
+                if (!p.active[k]) continue;
+                const Inst &in = p.inst[k];
+                if constexpr (FX) {
+                    I128 sa;
+                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) i128_add(sa, p.part[((uint64_t)k * G + b) * 3]);
+                    sa = block_sum128(sa);
+                    if (threadIdx.x == 0) s_ab[0] = pdx::dd_value(pdx::dd_of_i128(sa, -2 * in.F));
+                } else {
+                    double sa = 0.0;
                     for (unsigned b = threadIdx.x; b < G; b += blockDim.x)
-                        s += reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3)[0];
-                    s = block_sum_d(s);
-                    if (threadIdx.x == 0) s_ab[0] = s;
-                    __syncthreads();
-                    const double al = s_ab[0];
-                    const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
-                    double *w = V + iw * p.stride, *v = V + iv * p.stride;
+                        sa += reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3)[0];
+                    sa = block_sum_d(sa);
+                    if (threadIdx.x == 0) s_ab[0] = sa;
+                }
+                __syncthreads();
+                const double al = s_ab[0];
+                const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
+                T *w = V + iw * p.stride;
+                const T *v = V + iv * p.stride;
+                if constexpr (FX) {
+                    const FxCoef ca = fx_coef_dev(al);
+                    I128 acc;
+                    slice_x4(e0, e1, [&](uint64_t e) {
+                        const int64_t wi = w[e] - fx_mul(v[e], ca.K, ca.G);
+                        w[e] = wi;
+                        i128_add_prod(acc, wi, wi);
+                    });
+                    acc = block_sum128(acc);
+                    if (threadIdx.x == 0) p.part[((uint64_t)k * G + blockIdx.x) * 3 + 1] = acc;
+                } else {
                     double acc = 0.0;
-                    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+                    slice_x4(e0, e1, [&](uint64_t e) {
                         const double wi = w[e] - al * v[e];
                         w[e] = wi;
                         acc = fma(wi, wi, acc);
-                    }
+                    });
                     acc = block_sum_d(acc);
-                    if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3)[2] = acc;
-                    __syncthreads();
+                    if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3 + 1)[0] = acc;
                 }
+                __syncthreads();
             }
-            if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
         }
+        if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
         // ---------------- phase C: alpha, beta; w = (w - alpha v) / beta; checks ----------------
         const bool check = (j + 1) % p.check_every == 0;
         if (c0 < c1) {
@@ -548,14 +584,18 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_lanczos(PState p) {
                 if (!p.active[k]) continue;
                 const Inst &in = p.inst[k];
                 if constexpr (FX) {
-                    I128 t[3];
-                    for (int q = 0; q < 3; ++q) {
-                        I128 s;
-                        for (unsigned b = threadIdx.x; b < G; b += blockDim.x)
-                            i128_add(s, p.part[((uint64_t)k * G + b) * 3 + q]);
-                        t[q] = block_sum128(s);
+                    I128 sa, sb;
+                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
+                        i128_add(sa, p.part[((uint64_t)k * G + b) * 3]);
+                        i128_add(sb, p.part[((uint64_t)k * G + b) * 3 + 1]);
                     }
-                    if (threadIdx.x == 0) pdx::fx_alpha_beta(t, in.F, &s_ab[0], &s_ab[1]);
+                    sa = block_sum128(sa);
+                    sb = block_sum128(sb);
+                    if (threadIdx.x == 0) {
+                        s_ab[0] = pdx::dd_value(pdx::dd_of_i128(sa, -2 * in.F));
+                        const double b2 = pdx::dd_value(pdx::dd_of_i128(sb, -2 * in.F));
+                        s_ab[1] = b2 > 0.0 ? sqrt(b2) : 0.0;
+                    }
                 } else {
                     double sa = 0.0, sb = 0.0;
                     for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
@@ -579,14 +619,12 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_lanczos(PState p) {
                 }
                 const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
                 T *w = V + iw * p.stride;
-                const T *v = V + iv * p.stride;
                 if constexpr (FX) {
-                    const FxCoef ca = fx_coef_dev(al), cf = fx_coef_dev(be != 0.0 ? 1.0 / be : 0.0);
-                    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-                        w[e] = fx_mul(w[e] - fx_mul(v[e], ca.K, ca.G), cf.K, cf.G);
+                    const FxCoef cf = fx_coef_dev(be != 0.0 ? 1.0 / be : 0.0);
+                    slice_x4(e0, e1, [&](uint64_t e) { w[e] = fx_mul(w[e], cf.K, cf.G); });
                 } else {
                     const double f = be != 0.0 ? 1.0 / be : 0.0;
-                    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) w[e] *= f;
+                    slice_x4(e0, e1, [&](uint64_t e) { w[e] *= f; });
                 }
                 const bool last = j + 1 >= p.maxit;
                 if (owner && (check || be == 0.0 || (uint64_t)(j + 1) >= in.D || last)) {

@@ -115,6 +115,8 @@ __device__ __forceinline__ DD dd_of_i128(I128 s, int sh) {
     return dd_add(r, {l0, 0.0});
 }
 
+__device__ __forceinline__ double dd_value(DD x) { return x.h + x.l; }
+
 // alpha and beta of a fixed-point Lanczos step from the exact sums
 // t[0] = <w, v>, t[1] = <w, w>, t[2] = <v, v> of integer vectors with F fractional bits
 __device__ __forceinline__ void fx_alpha_beta(const I128 (&t)[3], int F, double *alpha, double *beta) {

@@ -268,6 +268,17 @@ __global__ void k_reduce(const double *__restrict__ partials, int nb, double *__
     if (threadIdx.x == 0) out[blockIdx.x] = mode == 1 ? sqrt(s) : s;
 }
 
+// y = sum_k c_k V_k over m stored float32 vectors, accumulated in float64 (the
+// Ritz vector of a float32 phase whose Krylov vectors were kept)
+__global__ void k_combine_f32(const float *__restrict__ V, uint64_t stride, int m, const double *__restrict__ c,
+                              float *__restrict__ y, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc = fma(c[k], (double)V[(uint64_t)k * stride + i], acc);
+        y[i] = (float)acc;
+    }
+}
+
 // y += c * v, float32 storage (Ritz vector assembly)
 __global__ void k_axpy_scalar_f32(float *__restrict__ y, const float *__restrict__ v, float c, uint64_t n) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
@@ -558,6 +569,8 @@ Layout make_layout(hb_handle h, const hb_lanczos_opts &o) {
     // scalars: alpha[maxit+1], beta[maxit+1], coef[maxit+1], misc[8]
     L.vec = L.scal + align256((uint64_t)(3 * (o.maxit + 1) + 8) * 8);
     L.nvec = o.reorth ? o.maxit + 1 : 3;
+    if (o.vec_dtype == HB_F32 && o.fp64_finish && !o.reorth && o.store_basis > 0)
+        L.nvec = std::min(o.maxit, o.store_basis) + 1;  // the float32 phase keeps v_0 .. v_K
     const uint64_t vbytes = align256(D * es);
     L.vec2 = L.vec + vbytes * L.nvec;
     L.nvec2 = 0;
@@ -666,11 +679,12 @@ struct PhaseResult {
 };
 
 // One Lanczos run.  V: base of the vector slots (slot stride `stride` elements);
-// slot 0 must hold the normalised start vector.  reorth: slot j holds v_j.
-// Otherwise three rotating slots.  Stops on tol (if tol > 0) or maxit.
+// slot 0 must hold the normalised start vector.  reorth or keep: slot j holds
+// v_j (keep: the three-term recurrence, the vectors only stored).  Otherwise
+// three rotating slots.  Stops on tol (if tol > 0) or maxit.
 template <typename T>
 hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, bool reorth, double tol, int check,
-                      PhaseResult &out) {
+                      PhaseResult &out, bool keep = false) {
     out = PhaseResult();
     std::vector<double> ha(maxit + 1), hb(maxit + 1);
     int iv = 0, ip = -1, iw = 1;  // slots of v_j, v_{j-1}, w
@@ -728,7 +742,7 @@ hb_status lanczos_run(Solve &s, hb_dtype dt, T *V, uint64_t stride, int maxit, b
             }
         }
         if (reorth || !kScalesInStep<T>) scale_any<T>(s, w, s.d_beta + j);
-        if (reorth) {
+        if (reorth || keep) {  // slot j holds v_j
             ip = iv;
             iv = j + 1;
             iw = j + 2;
@@ -973,13 +987,25 @@ hb_status lanczos_ground_state(hb_handle h, const hb_lanczos_opts *o, const void
         // keep a copy of the normalised start: the Ritz vector is regenerated from it
         float *start_copy = finish ? reinterpret_cast<float *>(ws + L.vec2) : nullptr;
         if (finish) k_copy_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(V, start_copy, D);
-        st = lanczos_run<float>(s, HB_F32, V, stride, o->maxit, reorth, tol32, o->check_every, r);
+        const bool keep = finish && o->store_basis > 0;
+        const int maxit32 = keep ? std::min(o->maxit, o->store_basis) : o->maxit;
+        st = lanczos_run<float>(s, HB_F32, V, stride, maxit32, reorth, tol32, o->check_every, r, keep);
         iters_f32 = r.iters;
         if (st == HB_OK && finish && !(r.converged && tol32 <= tol)) {
-            // Ritz vector of the float32 phase into slot 0, then continue in float64 / fixed point
+            // Ritz vector of the float32 phase, then continue in float64 / fixed point: one
+            // combination pass over the kept vectors, or a replay of the recurrence from the start
             const int m = r.iters;
-            if ((st = replay_ritz_f32(s, r, start_copy, V, stride)) != HB_OK) return st;
             float *y = V;
+            if (keep) {
+                std::vector<double> svec;
+                double th, sl;
+                tridiag_lowest_host(r.alpha.data(), r.beta.data(), m, &th, &sl, &svec);
+                PD_CUDA(cudaMemcpyAsync(s.d_coef, svec.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s.st));
+                y = start_copy;  // the start copy is not needed: the vectors are kept
+                k_combine_f32<<<s.grid_vec, kRedThreads, 0, s.st>>>(V, stride, m, s.d_coef, y, D);
+            } else if ((st = replay_ritz_f32(s, r, start_copy, V, stride)) != HB_OK) {
+                return st;
+            }
             PD_CUDA(cudaGetLastError());
             const uint64_t stride64 = align256(D * 8) / 8;
             const int rest = std::max(1, o->maxit - m);

@@ -161,6 +161,30 @@ def test_ring8_mixed_fx64_finish(env):
     h.close()
 
 
+@pytest.mark.parametrize("finish", ["fx64", "f64"])
+def test_mixed_with_kept_float32_basis(env, finish):
+    """The float32 phase keeps its Krylov vectors and forms its Ritz vector in one pass: the phase
+    is the same recurrence as with the replay (same alpha, beta, same step count), and the finish
+    reaches E0 within 1e-10 of the oracle."""
+    torch, pd = env
+    k = max(range(64), key=lambda i: wl.draw_batch_instances(64)[i].N_up * wl.draw_batch_instances(64)[i].N_dn)
+    inst = wl.draw_batch_instances(64)[k]
+    rec = golden("batch64")[k]
+    h = handle_for(inst.cluster, inst.U, inst.N_up, inst.N_dn)
+    r_rep = pd.lanczos_ground_state(h, maxit=600, tol=1e-10, dtype=torch.float32, fp64_finish=finish)
+    r_keep = pd.lanczos_ground_state(h, maxit=600, tol=1e-10, dtype=torch.float32, fp64_finish=finish,
+                                     store_basis=400)
+    assert r_keep.converged and r_keep.iterations_f32 == r_rep.iterations_f32 > 0
+    assert abs(r_keep.E0 - r_rep.E0) <= 1e-10 * max(1.0, abs(r_rep.E0))
+    assert close(r_keep.E0, rec["E0"])
+    # a cap below the phase's natural length ends the float32 phase early; the finish still converges
+    r_cap = pd.lanczos_ground_state(h, maxit=600, tol=1e-10, dtype=torch.float32, fp64_finish=finish,
+                                    store_basis=12)
+    assert r_cap.converged and r_cap.iterations_f32 == 12
+    assert abs(r_cap.E0 - r_rep.E0) <= 1e-10 * max(1.0, abs(r_rep.E0))
+    h.close()
+
+
 def test_fx64_step_tracks_f64_step(env):
     """Same start vector: alpha, beta of the fixed-point and float64 recurrences agree to ~1e-13."""
     torch, pd = env
