@@ -735,7 +735,7 @@ def run_learned(args, world, rank, local):
     for U in (2.0, 4.0, 6.0, 10.0):
         h = pd.Handle(cl.L, cl.bonds, cl.t, U, 8, 8)
         _, psi = learned.ground_state(h, tol=1e-6)
-        sets.append(learned.sample(h, psi, 500000, g))
+        sets.append(learned.sample(h, psi, 500000, seed=int(U)))
         del psi
         h.close()
     t_data = time.perf_counter() - t0

@@ -7,7 +7,9 @@
  * occupation bits of a combined basis state (bit i of (up << L) | dn, the
  * layout of Sec. III) to (log|psi|, sign logit):
  *     z1 = W1 x + b1, a1 = gelu(z1), z2 = W2 a1 + b2, a2 = gelu(z2), out = W3 a2 + b3,
- * hidden width 128, gelu the exact erf form.  Parameters are one float32
+ * hidden width 128, gelu the exact erf form (erf evaluated by Abramowitz &
+ * Stegun 7.1.28, |error| <= 3e-7, far below the bfloat16 rounding of the
+ * activations).  Parameters are one float32
  * vector in the order W1 [128 x n_in] row-major, b1 [128], W2 [128 x 128],
  * b2 [128], W3 [2 x 128], b3 [2]; matrix products run on the tensor cores
  * (tcgen05, bfloat16 operands, float32 accumulation).  All pointers are device
@@ -45,12 +47,26 @@ hb_status mlp_adam_step(hb_mlp_handle m, float lr, void *stream);
 /* Start vector over the whole basis of h (n_in must be 2L): v[I] = sign * exp(min(log|psi|, 10) - 10)
  * for every combined index I (states from the backward map), in dtype dt.  Not normalised. */
 hb_status mlp_start_vector(hb_mlp_handle m, hb_handle h, hb_dtype dt, void *v, void *stream);
+/* Training samples for the network: n basis states of h drawn with probability psi_I^2 / sum psi^2
+ * (inverse-CDF sampling over the whole basis; draw i is SplitMix64 output i + 1 of the stream seeded
+ * with `seed`, mapped to [0, 1)), written as combined strings (states, uint64 [n]) with the targets
+ * t_log = log|psi_I| minus its mean over the n draws and t_sign = +-1, after the global sign of psi
+ * is fixed so that its entry of largest magnitude (lowest index on ties) is positive.  psi: device
+ * float[D] (need not be normalised).  workspace: device buffer of mlp_sample_workspace_bytes bytes,
+ * 256-byte aligned.  Real-space handles only.  Asynchronous on `stream`. */
+hb_status mlp_sample_workspace_bytes(hb_handle h, uint64_t n, uint64_t *bytes);
+hb_status mlp_sample_training(hb_handle h, const float *psi, uint64_t n, uint64_t seed, uint64_t *states, float *t_log,
+                              float *t_sign, void *workspace, uint64_t workspace_bytes, void *stream);
 /* Sticky device error (HB_ERR_TIMEOUT if a tensor-core completion wait gave up); synchronises. */
 hb_status mlp_last_error(hb_mlp_handle m);
 /* Test entry: C[M x N] = A[M x K] B[N x K]^T, A and B bfloat16 row-major, C float32 row-major,
  * computed by the library's tcgen05 kernel (K multiple of 8, N = 32 or a multiple of 128).
  * Synchronises `stream`. */
 hb_status mlp_tc_gemm(const void *A, const void *B, float *C, int M, int N, int K, void *stream);
+
+/* Test entry: y[i] = gelu(x[i]) (deriv 0) or gelu'(x[i]) (deriv 1), the activation exactly as the
+ * network's kernels evaluate it (erf by Abramowitz & Stegun 7.1.28, |error| <= 3e-7).  Asynchronous. */
+hb_status mlp_activation(const float *x, uint64_t n, float *y, int32_t deriv, void *stream);
 
 /* Failure-detection self test (synchronous): a kernel waits, with the bounded
  * mbarrier wait used by the tensor-core kernels, on a barrier that nothing

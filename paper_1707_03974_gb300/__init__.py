@@ -6,7 +6,7 @@ Importing the package does not load the library; the first call does, and fails
 loudly if the library has not been built.
 """
 from ._binding import (HB_F32, HB_F64, HB_FX64, Batch, Handle, Inversion, Mlp, mlp_adam_step, mlp_forward, mlp_gradient,
-                       mlp_last_error, mlp_start_vector, mlp_tc_gemm, hb_device_wait_selftest, hubbard_autotune, hubbard_batch_apply,
+                       mlp_last_error, mlp_start_vector, mlp_tc_gemm, mlp_activation, mlp_sample_training, hb_device_wait_selftest, hubbard_autotune, hubbard_batch_apply,
                        hubbard_batch_autotune, lanczos_batch_ground_state, lanczos_batch_wait_selftest, hubbard_convert,
                        hubbard_fixed_point_bits, hubbard_get_hv_config, hubbard_set_hv_config, HubbardError, LanczosResult, hb_tridiag_lowest,  # noqa: F401
                        hubbard_apply, hubbard_basis_create, hubbard_basis_destroy, hubbard_last_error,
@@ -28,5 +28,5 @@ EXPORTED_SYMBOLS = ("hb_status_string", "hubbard_basis_create", "hubbard_basis_c
                     "paradeisos_inv_last_error", "lanczos_ritz_vector_f64", "hubbard_apply_c",
                     "hb_continued_fraction", "hb_measure_ceilings", "hubbard_apply_timed")
 MLP_SYMBOLS = ("mlp_create", "mlp_destroy", "mlp_param_count", "mlp_get_params", "mlp_set_params", "mlp_forward",
-               "mlp_gradient", "mlp_adam_step", "mlp_start_vector", "mlp_last_error", "mlp_tc_gemm",
+               "mlp_gradient", "mlp_adam_step", "mlp_start_vector", "mlp_last_error", "mlp_tc_gemm", "mlp_activation", "mlp_sample_workspace_bytes", "mlp_sample_training",
                "hb_device_wait_selftest")

@@ -117,6 +117,9 @@ def load():
         "mlp_start_vector": (ctypes.c_int, [P, P, I32, P, P]),
         "mlp_last_error": (ctypes.c_int, [P]),
         "mlp_tc_gemm": (ctypes.c_int, [P, P, P, I32, I32, I32, P]),
+        "mlp_activation": (ctypes.c_int, [P, U64, P, I32, P]),
+        "mlp_sample_workspace_bytes": (ctypes.c_int, [P, U64, ctypes.POINTER(U64)]),
+        "mlp_sample_training": (ctypes.c_int, [P, P, U64, U64, P, P, P, P, U64, P]),
         "hb_device_wait_selftest": (ctypes.c_int, [ctypes.c_uint32]),
         "hubbard_batch_create": (ctypes.c_int, [I32, P, ctypes.POINTER(P)]),
         "hubbard_batch_destroy": (ctypes.c_int, [P]),
@@ -654,6 +657,33 @@ def mlp_last_error(m: Mlp) -> str:
 
 def hb_device_wait_selftest(max_tries: int = 1000) -> str:
     return STATUS[load().hb_device_wait_selftest(int(max_tries))]
+
+
+def mlp_sample_training(h: Handle, psi, n: int, seed: int = 0, stream=None):
+    """(states int64, t_log float32, t_sign float32) of n basis states drawn with probability psi^2."""
+    import torch
+    _need_cuda(psi)
+    if psi.dtype != torch.float32 or psi.numel() != h.D:
+        raise ValueError("psi must be a float32 CUDA vector of D elements")
+    lib = load()
+    nb = ctypes.c_uint64()
+    _check(lib.mlp_sample_workspace_bytes(h.ptr, int(n), ctypes.byref(nb)), "mlp_sample_workspace_bytes")
+    ws = torch.empty((nb.value,), dtype=torch.uint8, device=psi.device)
+    states = torch.empty(n, dtype=torch.int64, device=psi.device)
+    t_log = torch.empty(n, dtype=torch.float32, device=psi.device)
+    t_sign = torch.empty(n, dtype=torch.float32, device=psi.device)
+    _check(lib.mlp_sample_training(h.ptr, _ptr(psi), int(n), int(seed) & ((1 << 64) - 1), _ptr(states), _ptr(t_log),
+                                   _ptr(t_sign), _ptr(ws), nb.value, _stream_ptr(stream)), "mlp_sample_training")
+    return states, t_log, t_sign
+
+
+def mlp_activation(x, deriv: bool = False, stream=None):
+    """gelu(x) or gelu'(x) of a float32 CUDA tensor, as the network's kernels evaluate it."""
+    import torch
+    _need_cuda(x)
+    y = torch.empty_like(x)
+    _check(load().mlp_activation(_ptr(x), x.numel(), _ptr(y), int(bool(deriv)), _stream_ptr(stream)), "mlp_activation")
+    return y
 
 
 def mlp_tc_gemm(A, B, stream=None):

@@ -451,7 +451,7 @@ __device__ __forceinline__ int inst_at(const Inst *inst, int n, uint64_t e) {
 // holds its first element; barrier.  With fixed-point vectors both reductions
 // are exact 128-bit sums (converted to float64 once, through double-double).
 template <int R, int NC, bool FX>
-__global__ void __launch_bounds__(kPThreads, (FX && NC <= 2) ? 4 : 3) k_batch_lanczos(PState p) {
+__global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) k_batch_lanczos(PState p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];  // filled by copy_inst, no constructor
     Inst &s_inst = *reinterpret_cast<Inst *>(s_inst_raw);
@@ -787,7 +787,7 @@ hb_status batch_hv_r(hb_batch *b, hb_dtype dt, const void *x, void *y, const int
 }
 
 hb_status batch_hv(hb_batch *b, hb_dtype dt, const void *x, void *y, const int *active, cudaStream_t st) {
-    if (b->rows == 4 && dt != HB_FX64) return batch_hv_r<4>(b, dt, x, y, active, st);
+    if (b->rows == 4) return batch_hv_r<4>(b, dt, x, y, active, st);
     if (b->rows == 1) return batch_hv_r<1>(b, dt, x, y, active, st);
     return batch_hv_r<2>(b, dt, x, y, active, st);
 }
@@ -871,7 +871,6 @@ hb_status hubbard_batch_autotune(hb_batch_handle b, hb_dtype dt, const void *x, 
     float best_ms = 3.4e38f;
     hb_status s = HB_OK;
     for (int R : {1, 2, 4}) {
-        if (R == 4 && dt == HB_FX64) continue;
         for (int T : {128, 256, 512}) {
             b->rows = R;
             b->threads = T;
@@ -992,7 +991,7 @@ hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, 
     int coop = 0;
     PD_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device));
     if (!coop) return HB_ERR_CUDA;
-    const int R = b->rows == 1 ? 1 : 2;  // rows per item of the persistent kernel (fixed point stages at most 2)
+    const int R = b->rows == 1 ? 1 : b->rows == 4 ? 4 : 2;  // rows per item: the batched H·v's tuned row count
     hb_status st = batch_prepare(b);
     if (st == HB_OK && R != b->rows) st = build_desc(b, R);  // items of R rows (batch_prepare rebuilds for apply)
     if (st != HB_OK) return st;
@@ -1000,7 +999,9 @@ hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, 
     const size_t smem = batch_smem(b, R, dt);
     void *kern = nullptr;
     int per_sm = 0;
-    st = R == 1 ? pick_persistent_r<1>(b, FX, smem, &kern, &per_sm) : pick_persistent_r<2>(b, FX, smem, &kern, &per_sm);
+    st = R == 1   ? pick_persistent_r<1>(b, FX, smem, &kern, &per_sm)
+         : R == 4 ? pick_persistent_r<4>(b, FX, smem, &kern, &per_sm)
+                  : pick_persistent_r<2>(b, FX, smem, &kern, &per_sm);
     if (st != HB_OK) return st;
     if (per_sm < 1) return HB_ERR_NO_MEMORY;
     const unsigned grid = (unsigned)std::min(per_sm * b->sm_count, L.gmax);

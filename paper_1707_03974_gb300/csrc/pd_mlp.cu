@@ -3,7 +3,8 @@
 // re-uses the method's own ground states as training data).
 //
 //   z1 = W1 x + b1, a1 = gelu(z1), z2 = W2 a1 + b2, a2 = gelu(z2), out = W3 a2 + b3
-//   out = (log|psi|, sign logit),  hidden width 128, gelu in the exact erf form.
+//   out = (log|psi|, sign logit),  hidden width 128, gelu in the exact erf form
+//   (erf evaluated by Abramowitz & Stegun 7.1.28, |error| <= 3e-7).
 //
 // Weights are kept in float32 (master copy, Adam) and used as bfloat16; the two
 // 128-wide matrix products of the forward pass, and the activation-gradient and
@@ -129,9 +130,36 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const __nv_bfloat16 *__restrict
 // ---------------------------------------------------------------------------
 // element-wise kernels
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// erf(x) by formula 7.1.28 of Abramowitz & Stegun, Handbook of Mathematical
+// Functions (1964): for x >= 0, erf(x) = 1 - (1 + a1 x + ... + a6 x^6)^-16 with
+// |error| <= 3e-7, odd in x.  The argument is clamped at 6, where erf is 1 to
+// float32 precision, so the power never overflows.  One reciprocal and about
+// thirteen float32 operations: the GELU of the network stays the exact-erf
+// form to far inside bfloat16 resolution (2^-8 relative) at a fraction of the
+// cost of erff.
+__device__ __forceinline__ float erf_as7128(float x) {
+    const float ax = fminf(fabsf(x), 6.0f);
+    float p = fmaf(ax, 0.0000430638f, 0.0002765672f);
+    p = fmaf(ax, p, 0.0001520143f);
+    p = fmaf(ax, p, 0.0092705272f);
+    p = fmaf(ax, p, 0.0422820123f);
+    p = fmaf(ax, p, 0.0705230784f);
+    p = fmaf(ax, p, 1.0f);
+    p = p * p;  // ^2
+    p = p * p;  // ^4
+    p = p * p;  // ^8
+    p = p * p;  // ^16
+    return copysignf(1.0f - __fdividef(1.0f, p), x);
+}
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erf_as7128(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float x) {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+    return 0.5f * (1.0f + erf_as7128(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+
+// y = gelu(x) (deriv 0) or gelu'(x) (deriv 1): the activation as the network's kernels evaluate it
+__global__ void k_activation(const float *__restrict__ x, uint64_t n, float *__restrict__ y, int deriv) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        y[i] = deriv ? gelu_grad_f(x[i]) : gelu_f(x[i]);
 }
 
 // x rows: bit i of the combined state -> column i (0/1), columns >= n_bits zero.
@@ -468,6 +496,219 @@ __global__ void __launch_bounds__(128) k_mlp_start(const __nv_bfloat16 *__restri
 }
 int grid_of(uint64_t n, int sms) { return (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8)); }
 
+// ---------------------------------------------------------------------------
+// Training samples: basis states drawn with probability psi^2 (inverse-CDF
+// sampling over the whole basis).  psi is cut into blocks of kSampBlock
+// entries; the float64 block sums of psi^2 are scanned into block offsets, a
+// draw u in [0, total) picks its block by binary search and its entry by a
+// warp-wide scan inside the block.  The draws are SplitMix64 outputs (Steele,
+// Lea & Flood 2014), draw i = output i + 1 of the stream seeded with `seed`,
+// mapped to (z >> 11) 2^-53 in [0, 1).  The global sign is fixed so that the
+// entry of largest |psi| (lowest index on ties) is positive.
+constexpr int kSampBlock = 1024;
+constexpr uint64_t kGammaS = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ double splitmix_unit(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * kGammaS;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// (value, index) of the larger |psi|, the lower index on ties
+__device__ __forceinline__ void argmax_merge(float &a, uint64_t &ia, float b, uint64_t ib) {
+    if (b > a || (b == a && ib < ia)) {
+        a = b;
+        ia = ib;
+    }
+}
+
+// one CTA per block: sum of psi^2 in float64 (fixed tree order) and the block's argmax |psi|
+__global__ void __launch_bounds__(256) k_samp_blocks(const float *__restrict__ psi, uint64_t D, double *bsum,
+                                                     float *bmax, uint64_t *bidx) {
+    __shared__ double s_sum[8];
+    __shared__ float s_max[8];
+    __shared__ uint64_t s_idx[8];
+    const uint64_t b = blockIdx.x, e0 = b * kSampBlock;
+    double acc = 0.0;
+    float mx = -1.f;
+    uint64_t mi = UINT64_MAX;
+    for (int k = threadIdx.x; k < kSampBlock; k += blockDim.x) {
+        const uint64_t e = e0 + k;
+        if (e < D) {
+            const double v = psi[e];
+            acc = fma(v, v, acc);
+            argmax_merge(mx, mi, fabsf(psi[e]), e);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        const float m2 = __shfl_down_sync(0xffffffffu, mx, o);
+        const uint64_t i2 = __shfl_down_sync(0xffffffffu, mi, o);
+        argmax_merge(mx, mi, m2, i2);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_sum[w] = acc;
+        s_max[w] = mx;
+        s_idx[w] = mi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        float m = -1.f;
+        uint64_t i = UINT64_MAX;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            t += s_sum[k];
+            argmax_merge(m, i, s_max[k], s_idx[k]);
+        }
+        bsum[b] = t;
+        bmax[b] = m;
+        bidx[b] = i;
+    }
+}
+
+// one CTA: bsum -> exclusive prefix (in place), total, and the global sign of psi
+__global__ void __launch_bounds__(1024) k_samp_scan(double *bsum, const float *bmax, const uint64_t *bidx,
+                                                    uint64_t nblk, const float *__restrict__ psi, double *misc) {
+    __shared__ double s_part[1024];
+    __shared__ float s_max[1024];
+    __shared__ uint64_t s_idx[1024];
+    const uint64_t per = (nblk + blockDim.x - 1) / blockDim.x;
+    const uint64_t b0 = min(nblk, threadIdx.x * per), b1 = min(nblk, b0 + per);
+    double t = 0.0;
+    float m = -1.f;
+    uint64_t mi = UINT64_MAX;
+    for (uint64_t b = b0; b < b1; ++b) {
+        t += bsum[b];
+        argmax_merge(m, mi, bmax[b], bidx[b]);
+    }
+    s_part[threadIdx.x] = t;
+    s_max[threadIdx.x] = m;
+    s_idx[threadIdx.x] = mi;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // sequential scan of 1024 partials: fixed order
+        double run = 0.0;
+        float gm = -1.f;
+        uint64_t gi = UINT64_MAX;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const double pk = s_part[k];
+            s_part[k] = run;
+            run += pk;
+            argmax_merge(gm, gi, s_max[k], s_idx[k]);
+        }
+        misc[0] = run;                                         // total
+        misc[1] = (gi != UINT64_MAX && psi[gi] < 0.f) ? -1.0 : 1.0;  // global sign
+    }
+    __syncthreads();
+    double run = s_part[threadIdx.x];
+    for (uint64_t b = b0; b < b1; ++b) {
+        const double pb = bsum[b];
+        bsum[b] = run;
+        run += pb;
+    }
+}
+
+// one warp per sample: block by binary search over the offsets, entry by a warp scan in the block
+__global__ void __launch_bounds__(256) k_samp_draw(const float *__restrict__ psi, uint64_t D, const double *bpre,
+                                                   uint64_t nblk, const double *misc, uint64_t n, uint64_t seed,
+                                                   const uint32_t *__restrict__ str_up,
+                                                   const uint32_t *__restrict__ str_dn, uint64_t D_dn, int L,
+                                                   uint64_t *states, double *logs, float *t_sign) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const double total = misc[0], gsign = misc[1];
+    for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const double u = splitmix_unit(seed, i) * total;
+        uint64_t lo = 0, hi = nblk - 1;  // largest b with bpre[b] <= u
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (bpre[mid] <= u) lo = mid; else hi = mid - 1;
+        }
+        const uint64_t e0 = lo * kSampBlock;
+        const double r = u - bpre[lo];
+        // lane l covers entries e0 + 32 l .. e0 + 32 l + 31
+        double part = 0.0;
+        for (int k = 0; k < 32; ++k) {
+            const uint64_t e = e0 + (uint64_t)lane * 32 + k;
+            if (e < D) {
+                const double v = psi[e];
+                part = fma(v, v, part);
+            }
+        }
+        double incl = part;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const double excl = incl - part;
+        const unsigned hit = __ballot_sync(0xffffffffu, incl > r);
+        // the lane whose range holds r (rounding can leave r past the last sum: take the last lane)
+        const int owner = hit ? __ffs(hit) - 1 : 31;
+        uint64_t idx = UINT64_MAX;
+        if (lane == owner) {
+            double run = excl;
+            uint64_t last = UINT64_MAX;
+            for (int k = 0; k < 32; ++k) {
+                const uint64_t e = e0 + (uint64_t)lane * 32 + k;
+                if (e >= D) break;
+                const double v = psi[e];
+                if (v != 0.0) last = e;
+                run = fma(v, v, run);
+                if (run > r && v != 0.0) {
+                    idx = e;
+                    break;
+                }
+            }
+            if (idx == UINT64_MAX) idx = last;
+        }
+        idx = __shfl_sync(0xffffffffu, idx, owner);
+        if (idx == UINT64_MAX) {  // an all-zero stretch: the block's last nonzero entry below
+            for (uint64_t e = min(D, e0 + kSampBlock); e > 0 && idx == UINT64_MAX; --e)
+                if (psi[e - 1] != 0.f) idx = e - 1;
+            if (idx == UINT64_MAX) idx = 0;
+        }
+        if (lane == 0) {
+            const uint64_t uu = idx / D_dn, dd = idx - uu * D_dn;
+            states[i] = ((uint64_t)str_up[uu] << L) | (uint64_t)str_dn[dd];
+            const double amp = gsign * (double)psi[idx];
+            logs[i] = log(fabs(amp) > 0.0 ? fabs(amp) : 1e-300);
+            t_sign[i] = amp >= 0.0 ? 1.f : -1.f;
+        }
+    }
+}
+
+// t_log = logs - mean(logs), mean in float64 over a fixed order (one CTA)
+__global__ void __launch_bounds__(1024) k_samp_center(const double *logs, uint64_t n, float *t_log) {
+    __shared__ double s_w[32];
+    __shared__ double s_mean;
+    double acc = 0.0;
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) acc += logs[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_w[k];
+        s_mean = t / (double)n;
+    }
+    __syncthreads();
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) t_log[i] = (float)(logs[i] - s_mean);
+}
+
+uint64_t align256u(uint64_t x) { return (x + 255) & ~255ull; }
+
+void samp_layout(uint64_t D, uint64_t n, uint64_t *o_bmax, uint64_t *o_bidx, uint64_t *o_logs, uint64_t *o_misc,
+                 uint64_t *total) {
+    const uint64_t nblk = (D + kSampBlock - 1) / kSampBlock;
+    *o_bmax = align256u(nblk * 8);
+    *o_bidx = *o_bmax + align256u(nblk * 4);
+    *o_logs = *o_bidx + align256u(nblk * 8);
+    *o_misc = *o_logs + align256u(n * 8);
+    *total = *o_misc + 256;
+}
+
 }  // namespace
 
 struct hb_mlp {
@@ -721,6 +962,41 @@ hb_status mlp_start_vector(hb_mlp_handle m, hb_handle h, hb_dtype dt, void *v, v
     return HB_OK;
 }
 
+hb_status mlp_sample_workspace_bytes(hb_handle h, uint64_t n, uint64_t *bytes) {
+    if (!h || !bytes || h->ks) return HB_ERR_INVALID_ARG;
+    uint64_t a, b, c, d;
+    samp_layout(h->D, n, &a, &b, &c, &d, bytes);
+    return HB_OK;
+}
+
+hb_status mlp_sample_training(hb_handle h, const float *psi, uint64_t n, uint64_t seed, uint64_t *states, float *t_log,
+                              float *t_sign, void *workspace, uint64_t workspace_bytes, void *stream) {
+    if (!h || !psi || !states || !t_log || !t_sign || !workspace || n == 0 || h->ks) return HB_ERR_INVALID_ARG;
+    if ((uintptr_t)workspace % 256 != 0) return HB_ERR_INVALID_ARG;
+    uint64_t o_bmax, o_bidx, o_logs, o_misc, total;
+    samp_layout(h->D, n, &o_bmax, &o_bidx, &o_logs, &o_misc, &total);
+    if (workspace_bytes < total) return HB_ERR_NO_MEMORY;
+    hb_status s = pd_build_tables(h);
+    if (s != HB_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    double *bsum = reinterpret_cast<double *>(ws);
+    float *bmax = reinterpret_cast<float *>(ws + o_bmax);
+    uint64_t *bidx = reinterpret_cast<uint64_t *>(ws + o_bidx);
+    double *logs = reinterpret_cast<double *>(ws + o_logs);
+    double *misc = reinterpret_cast<double *>(ws + o_misc);
+    const uint64_t nblk = (h->D + kSampBlock - 1) / kSampBlock;
+    if (nblk > 0x7FFFFFFFull) return HB_ERR_OVERFLOW;
+    k_samp_blocks<<<(unsigned)nblk, 256, 0, st>>>(psi, h->D, bsum, bmax, bidx);
+    k_samp_scan<<<1, 1024, 0, st>>>(bsum, bmax, bidx, nblk, psi, misc);
+    const unsigned grid = (unsigned)std::min<uint64_t>((n + 7) / 8, (uint64_t)h->sm_count * 16);
+    k_samp_draw<<<grid, 256, 0, st>>>(psi, h->D, bsum, nblk, misc, n, seed, h->up.str, h->dn.str, h->D_dn, h->L,
+                                      states, logs, t_sign);
+    k_samp_center<<<1, 1024, 0, st>>>(logs, n, t_log);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
 hb_status mlp_last_error(hb_mlp_handle m) {
     if (!m) return HB_ERR_INVALID_ARG;
     PD_CUDA(cudaDeviceSynchronize());
@@ -755,6 +1031,17 @@ hb_status hb_device_wait_selftest(uint32_t max_tries) {
 }
 
 // C[M, N] = A[M, K] B[N, K]^T on the tensor cores (bf16 in, f32 out), exposed for tests.
+hb_status mlp_activation(const float *x, uint64_t n, float *y, int32_t deriv, void *stream) {
+    if (!x || !y || (deriv != 0 && deriv != 1)) return HB_ERR_INVALID_ARG;
+    if (n == 0) return HB_OK;
+    int dev = 0, sms = 0;
+    PD_CUDA(cudaGetDevice(&dev));
+    PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    k_activation<<<grid_of(n, sms), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, n, y, deriv);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
 hb_status mlp_tc_gemm(const void *A, const void *B, float *C, int M, int N, int K, void *stream) {
     if (!A || !B || !C || M < 1 || N < 1 || K < 1 || K % 8 != 0 || (N != 32 && N % 128 != 0)) return HB_ERR_INVALID_ARG;
     hb_mlp tmp;

@@ -4,11 +4,10 @@ Not part of the paper.  The network (include/paradeisos_mlp.h) is trained on
 ground states that the library computes itself (float32 Lanczos + Ritz vector)
 at a few values of U, then used to build the start vector of the float64-grade
 Lanczos solve at other U or another sector.  Training samples are basis states
-drawn with probability |psi|^2 (inverse-CDF sampling), targets are
-log|psi| (shifted to zero mean per training problem) and the sign of psi with
-the global sign fixed by the largest entry.  Everything numerical runs in the
-library's kernels; torch provides memory, random numbers and the sampling
-bookkeeping.
+drawn with probability |psi|^2 by the library's inverse-CDF sampler, targets
+are log|psi| (shifted to zero mean per training problem) and the sign of psi
+with the global sign fixed by the largest entry.  Everything numerical runs in
+the library's kernels; torch provides memory and the random mini-batch choice.
 """
 from __future__ import annotations
 
@@ -38,21 +37,10 @@ def ground_state(h: B.Handle, tol: float = 1e-6, maxit: int = 2000, seed: int = 
     return E0, psi
 
 
-def sample(h: B.Handle, psi, n: int, generator) -> TrainingSet:
-    """n basis states drawn with probability psi^2, with their log-amplitude and sign targets."""
-    import torch
-    p = psi.double()
-    k = int(torch.argmax(p.abs()).item())
-    if p[k] < 0:
-        p = -p
-    cdf = torch.cumsum(p * p, 0)
-    u = torch.rand(n, generator=generator, device=psi.device, dtype=torch.float64) * cdf[-1]
-    idx = torch.searchsorted(cdf, u).clamp_(max=h.D - 1)
-    states = B.paradeisos_unrank(h, idx.to(torch.int64))
-    amp = p[idx]
-    t_log = torch.log(amp.abs().clamp_min(1e-300))
-    t_log = (t_log - t_log.mean()).float()
-    t_sign = torch.where(amp >= 0, 1.0, -1.0).float()
+def sample(h: B.Handle, psi, n: int, seed: int = 0) -> TrainingSet:
+    """n basis states drawn with probability psi^2, with their log-amplitude and sign targets
+    (the library's inverse-CDF sampler, mlp_sample_training)."""
+    states, t_log, t_sign = B.mlp_sample_training(h, psi.float().contiguous(), n, seed)
     return TrainingSet(states, t_log, t_sign)
 
 

@@ -20,7 +20,7 @@ def test_learned_start_gains_over_random_start():
     for U in (3.0, 8.0):
         h = handle_for(cl, U, 6, 6)
         _, psi = learned.ground_state(h, tol=1e-6)
-        sets.append(learned.sample(h, psi, 200000, g))
+        sets.append(learned.sample(h, psi, 200000, seed=int(U)))
         h.close()
     m = pd.Mlp(24, seed=1)
     rep = learned.train(m, sets, steps=3000, batch=16384, lr=2e-3)
@@ -38,4 +38,41 @@ def test_learned_start_gains_over_random_start():
     assert res["learned_f64"]["iterations"] < rnd
     assert res["learned_fx64"]["iterations"] < rnd + 5
     h.close()
+    m.close()
+
+
+def test_learned_start_on_the_4x4_workload():
+    """The learned-start configuration itself: the 4x4 t-t' cluster (D = 165,636,900), the network
+    trained on the library's own ground states at U = 2, 4, 6, 10 (half filling), then used at the
+    unseen U = 5 and in the doped (7,7) sector at U = 8.  Fixed-point Lanczos from the learned start
+    must need fewer steps than from the better of two random starts, and reach the same E0 as the
+    float64 random-start solve to 1e-10."""
+    torch = need_gpu()
+    import paper_1707_03974_gb300 as pd
+    from paper_1707_03974_gb300 import learned
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    sets = []
+    for U in (2.0, 4.0, 6.0, 10.0):
+        h = handle_for(cl, U, 8, 8)
+        _, psi = learned.ground_state(h, tol=1e-6)
+        sets.append(learned.sample(h, psi, 500000, seed=int(U)))
+        del psi
+        h.close()
+        torch.cuda.empty_cache()
+    m = pd.Mlp(32, seed=1)
+    rep = learned.train(m, sets, steps=600, batch=32768, lr=2e-3)
+    assert rep.losses[-1] < rep.losses[0]
+    assert pd.mlp_last_error(m) == "HB_OK"
+    for U, nu, nd in ((5.0, 8, 8), (8.0, 7, 7)):
+        h = handle_for(cl, U, nu, nd)
+        ref = learned.solve_from(h, torch.float64, seed=0)
+        rnd = [learned.solve_from(h, torch.int64, seed=s)["iterations"] for s in (0, 1)]
+        v0 = pd.mlp_start_vector(m, h, torch.int64)
+        got = learned.solve_from(h, torch.int64, v0=v0)
+        del v0
+        assert ref["converged"] and got["converged"]
+        assert abs(got["E0"] - ref["E0"]) <= 1e-10 * abs(ref["E0"]), (U, nu, got["E0"], ref["E0"])
+        assert got["iterations"] < min(rnd), (U, nu, got["iterations"], rnd)
+        h.close()
+        torch.cuda.empty_cache()
     m.close()
