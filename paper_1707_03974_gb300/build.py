@@ -34,8 +34,9 @@ def _stale(lib: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "pd_common.cuh"), os.path.join(CSRC, "pd_hv_body.cuh"), os.path.join(CSRC, "pd_hv_f32wb.cuh"), os.path.join(CSRC, "pd_wb_sched.h"), os.path.join(CSRC, "pd_tc.cuh"), os.path.join(ROOT, "include", "paradeisos_mlp.h"),
-                                                       os.path.join(ROOT, "include", "paradeisos.h")]
+    import glob
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
+        sorted(glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
     if not force and not _stale(LIB, deps):
         return LIB
     os.makedirs(OUTDIR, exist_ok=True)

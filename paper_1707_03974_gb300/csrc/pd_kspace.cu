@@ -337,18 +337,22 @@ __global__ void __launch_bounds__(256) k_k_hv(KHv p, const T *__restrict__ x, T 
 // fixed point every partial sum is an exact integer sum, so the result is the
 // same integer as the pairwise form's.
 template <typename T, int JM>
-__global__ void __launch_bounds__(256) k_k_hv_rows(KHv p, const T *__restrict__ x, T *__restrict__ y) {
+__global__ void __launch_bounds__(512) k_k_hv_rows(KHv p, const T *__restrict__ x, T *__restrict__ y,
+                                                     uint32_t maxlen) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = p.a.N, nu = p.a.nu, nd = p.a.nd;
     uint64_t *s_up = reinterpret_cast<uint64_t *>(smem);
     const size_t nup = (size_t)(N - 1) * (nu > 0 ? nu : 1);
     uint8_t *s_cnt = reinterpret_cast<uint8_t *>(s_up + nup);
-    T *s_t = reinterpret_cast<T *>(smem + ((nup * 8 + 32 + 15) & ~(size_t)15));
+    // two buffers of the per-q row sums: t_q is built in buffer q % 2 while other
+    // threads may still read t_{q-1} from the other one, so one barrier per q suffices
+    T *s_t0 = reinterpret_cast<T *>(smem + ((nup * 8 + 32 + 15) & ~(size_t)15));
+    T *s_t1 = s_t0 + maxlen;
     for (uint64_t r = blockIdx.x; r < p.Dup; r += gridDim.x) {
         const int kd = (int)p.rowKd[r];
-        const uint64_t len = p.doff[kd + 1] - p.doff[kd];
+        const uint32_t len = (uint32_t)(p.doff[kd + 1] - p.doff[kd]);
         if (len == 0) continue;  // uniform across the CTA
-        __syncthreads();
+        __syncthreads();  // the previous row is done with shared memory
         for (int e = threadIdx.x; e < (N - 1) * nu; e += blockDim.x) s_up[e] = p.upmov[r * (uint64_t)(N - 1) * nu + e];
         if (threadIdx.x < N - 1) s_cnt[threadIdx.x] = p.upcnt[r * (uint64_t)(N - 1) + threadIdx.x];
         __syncthreads();
@@ -358,14 +362,15 @@ __global__ void __launch_bounds__(256) k_k_hv_rows(KHv p, const T *__restrict__ 
         T acc_f[JM];
 #pragma unroll
         for (int i = 0; i < JM; ++i) acc_i[i] = 0, acc_f[i] = T(0);
+        int buf = 0;
         for (int q = 1; q < N; ++q) {
             const int cu = s_cnt[q - 1];
             if (cu == 0) continue;  // uniform
             const int kd2 = ksub(p.a.Lx, p.a.Ly, kd, q);
-            const uint64_t len2 = p.doff[kd2 + 1] - p.doff[kd2];
+            const uint32_t len2 = (uint32_t)(p.doff[kd2 + 1] - p.doff[kd2]);
             const uint64_t *ua = s_up + (size_t)(q - 1) * nu;
-            __syncthreads();  // the previous q is done with s_t
-            for (uint64_t e = threadIdx.x; e < len2; e += blockDim.x) {
+            T *s_t = buf ? s_t1 : s_t0;
+            for (uint32_t e = threadIdx.x; e < len2; e += blockDim.x) {
                 T t = T(0);
                 for (int a = 0; a < cu; ++a) {
                     const uint64_t m = ua[a];
@@ -375,13 +380,16 @@ __global__ void __launch_bounds__(256) k_k_hv_rows(KHv p, const T *__restrict__ 
                 s_t[e] = t;
             }
             __syncthreads();
+            const uint8_t *dcq = dc + (uint64_t)(q - 1) * len;
+            const uint32_t *dmq = dm + (uint64_t)(q - 1) * nd * len;
 #pragma unroll
             for (int i = 0; i < JM; ++i) {
-                const uint64_t j = threadIdx.x + (uint64_t)i * blockDim.x;
+                const uint32_t j = threadIdx.x + (uint32_t)i * blockDim.x;
                 if (j >= len) break;
-                const int cd = dc[(uint64_t)(q - 1) * len + j];
+                const int cd = dcq[j];
+                const uint32_t *dmj = dmq + j;
                 for (int b = 0; b < cd; ++b) {
-                    const uint32_t ev = dm[((uint64_t)(q - 1) * nd + b) * len + j];
+                    const uint32_t ev = dmj[(uint64_t)b * len];
                     const T v = s_t[ev & 0x7FFFFFFFu];
                     if constexpr (std::is_same<T, int64_t>::value) {
                         const int64_t mneg = -(int64_t)(ev >> 31);
@@ -391,12 +399,13 @@ __global__ void __launch_bounds__(256) k_k_hv_rows(KHv p, const T *__restrict__ 
                     }
                 }
             }
+            buf ^= 1;
         }
         const uint64_t F = p.rowF[r], e0 = p.doff[kd];
         const double eur = p.eu[r];
 #pragma unroll
         for (int i = 0; i < JM; ++i) {
-            const uint64_t j = threadIdx.x + (uint64_t)i * blockDim.x;
+            const uint32_t j = threadIdx.x + (uint32_t)i * blockDim.x;
             if (j >= len) break;
             const double diag = eur + p.ed[e0 + j] + p.U_diag;
             const T xI = x[F + j];
@@ -657,14 +666,16 @@ namespace {
 template <typename T, int JM>
 hb_status launch_rows(hb_handle h, const KHv &p, const T *x, T *y, cudaStream_t st, uint64_t maxlen) {
     const size_t nup = (size_t)(h->ks->N - 1) * std::max(h->ks->nu, 1);
-    const size_t smem = ((nup * 8 + 32 + 15) & ~(size_t)15) + (size_t)maxlen * sizeof(T);
+    const size_t smem = ((nup * 8 + 32 + 15) & ~(size_t)15) + 2 * (size_t)maxlen * sizeof(T);
+    // threads: the fewest warps whose JM column slots cover the longest row, so no slot sits idle
+    const int threads = (int)std::min<uint64_t>(512, std::max<uint64_t>(64, (maxlen + JM * 32 - 1) / (JM * 32) * 32));
     auto kern = k_k_hv_rows<T, JM>;
     PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return HB_ERR_NO_MEMORY;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(h->ks->Dup, (uint64_t)per_sm * h->sm_count));
-    kern<<<grid, 256, smem, st>>>(p, x, y);
+    kern<<<grid, threads, smem, st>>>(p, x, y, (uint32_t)maxlen);
     PD_CUDA(cudaGetLastError());
     return HB_OK;
 }
@@ -675,8 +686,8 @@ hb_status k_apply_t(hb_handle h, const T *x, T *y, cudaStream_t st) {
     uint64_t maxlen = 0;
     for (int k = 0; k < h->ks->N; ++k) maxlen = std::max(maxlen, h->ks->h_doff[k + 1] - h->ks->h_doff[k]);
     // row-factorised form while a row fits the per-thread accumulators and shared memory
-    if (maxlen <= 4 * 256 && maxlen * sizeof(T) <= 96 * 1024) return launch_rows<T, 4>(h, p, x, y, st, maxlen);
-    if (maxlen <= 16 * 256 && maxlen * sizeof(T) <= 96 * 1024) return launch_rows<T, 16>(h, p, x, y, st, maxlen);
+    if (maxlen <= 4 * 512 && 2 * maxlen * sizeof(T) <= 96 * 1024) return launch_rows<T, 4>(h, p, x, y, st, maxlen);
+    if (maxlen <= 16 * 512 && 2 * maxlen * sizeof(T) <= 192 * 1024) return launch_rows<T, 16>(h, p, x, y, st, maxlen);
     constexpr int kWarps = 8;  // pairwise form, one row per warp
     const size_t smem = (size_t)kWarps * ((size_t)(h->ks->N - 1) * std::max(h->ks->nu, 1) * 8 + 32);
     const unsigned grid =

@@ -32,35 +32,56 @@ constexpr uint32_t kWaitTries = 1u << 24;
 // ---------------------------------------------------------------------------
 // Generic tcgen05 GEMM:  C[M, N] (+)= A[M, K] * B[N, K]^T  (A, B bf16 row-major,
 // K contiguous; C f32 row-major).  One CTA of 128 threads per 128 x BN tile and
-// K range; the tiles are copied to shared memory in the core-matrix layout, one
-// thread issues the MMAs, the accumulator lives in tensor memory and the four
-// warps read it back (warp w owns rows 32w .. 32w+31).  mode 0: C = acc,
-// mode 1: atomicAdd(C, acc) (split K / accumulation).  Columns >= n_store are
-// not written.
+// K range.  The K range is cut into slabs of kBK; slab i is copied to shared
+// memory stage i % 2 in the core-matrix layout while the tensor core still
+// runs the MMAs of slab i - 1 from the other stage (one thread issues them and
+// commits them to the stage's mbarrier; a stage is refilled only after the
+// MMAs that read it have completed).  The accumulator lives in tensor memory
+// and the four warps read it back (warp w owns rows 32w .. 32w+31).  mode 0:
+// C = acc, mode 1: atomicAdd(C, acc) (split K / accumulation).  Columns >=
+// n_store are not written.  Dynamic shared memory: tc_gemm_smem(BN).
+__host__ __device__ constexpr size_t tc_stage_bytes(int BN) { return (size_t)(kBM + BN) * kBK * 2; }
+__host__ __device__ constexpr size_t tc_gemm_smem(int BN) { return 2 * tc_stage_bytes(BN) + 1024; }
+
 template <int BN>
 __global__ void __launch_bounds__(128) k_tc_gemm(const __nv_bfloat16 *__restrict__ A, int lda,
                                                  const __nv_bfloat16 *__restrict__ B, int ldb, float *C, int ldc,
                                                  int M, int N, int K, int k_per_cta, int n_store, int mode,
                                                  unsigned *err) {
-    __shared__ __align__(1024) uint8_t sA[kBM * kBK * 2];
-    __shared__ __align__(1024) uint8_t sB[BN * kBK * 2];
-    __shared__ __align__(8) uint64_t bar;
+    extern __shared__ __align__(1024) uint8_t smem_dyn[];
+    // 1024-byte aligned base for the operand stages
+    uint8_t *base = smem_dyn + ((1024 - (tc::smem_u32(smem_dyn) & 1023)) & 1023);
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_slot;
     constexpr uint32_t kCols = BN < 32 ? 32 : BN;
     constexpr uint32_t kSBO = (kBK / 8) * 128;  // bytes between 8-row groups
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(&tmem_slot, kCols);
-    if (tid == 0) tc::mbar_init(&bar, 1);
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
     const int kb = blockIdx.z * k_per_cta, ke = min(K, kb + k_per_cta);
+    const int nslab = ke > kb ? (ke - kb + kBK - 1) / kBK : 0;
     constexpr uint32_t idesc = tc::make_idesc_bf16(kBM, BN);
-    uint32_t phase = 0;
-    bool ok = true, any = false;
-    for (int k0 = kb; k0 < ke && ok; k0 += kBK) {
+    uint32_t phase[2] = {0, 0};
+    bool pending[2] = {false, false};
+    bool ok = true;
+    for (int i = 0; i < nslab && ok; ++i) {
+        const int st = i & 1, k0 = kb + i * kBK;
+        uint8_t *sA = base + st * tc_stage_bytes(BN), *sB = sA + (size_t)kBM * kBK * 2;
+        if (pending[st]) {  // the MMAs of slab i - 2 read this stage: wait before refilling it
+            ok = __syncthreads_and(tc::mbar_wait(&bar[st], phase[st], kWaitTries) ? 1 : 0) != 0;
+            if (!ok) break;  // the stage stays pending
+            phase[st] ^= 1;
+            pending[st] = false;
+            tc::fence_after_sync();
+        }
         // 16-byte chunks: row r, K-group kc (8 elements)
         for (int c = tid; c < kBM * (kBK / 8); c += 128) {
             const int r = c / (kBK / 8), kc = c % (kBK / 8);
@@ -86,24 +107,31 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const __nv_bfloat16 *__restrict
             for (int ks = 0; ks < kBK / 16; ++ks) {
                 const uint64_t ad = tc::make_desc(a0 + ks * 256, 128, kSBO);
                 const uint64_t bd = tc::make_desc(b0 + ks * 256, 128, kSBO);
-                tc::mma_bf16(tmem, ad, bd, idesc, (any || ks > 0) ? 1u : 0u);
+                tc::mma_bf16(tmem, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
             }
-            tc::commit(&bar);
+            tc::commit(&bar[st]);
         }
-        ok = tc::mbar_wait(&bar, phase, kWaitTries);
-        ok = __syncthreads_and(ok ? 1 : 0) != 0;  // uniform decision for the whole CTA
-        phase ^= 1;
-        any = true;
-        tc::fence_after_sync();
+        pending[st] = true;
     }
+    // the last commits: the accumulator is complete once every issued MMA has finished
+    for (int q = 0; q < 2 && ok; ++q) {
+        const int st = (nslab + q) & 1;  // older pending stage first
+        if (!pending[st]) continue;
+        ok = __syncthreads_and(tc::mbar_wait(&bar[st], phase[st], kWaitTries) ? 1 : 0) != 0;
+        if (!ok) break;
+        phase[st] ^= 1;
+        pending[st] = false;
+    }
+    tc::fence_after_sync();
     if (!ok) {
-        // gave up waiting: record it, then drain (bounded) so no MMA still writes the
-        // tensor memory released below
+        // a wait gave up: record it, then wait (bounded) once more on every stage still pending,
+        // so that no MMA still writes the tensor memory released below
         if (tid == 0) atomicOr(err, PD_ERRBIT(HB_ERR_TIMEOUT));
-        tc::mbar_wait(&bar, phase ^ 1, kWaitTries);
+        for (int st = 0; st < 2; ++st)
+            if (pending[st]) tc::mbar_wait(&bar[st], phase[st], kWaitTries);
         __syncthreads();
     }
-    if (ok && any) {
+    if (ok && nslab > 0) {
         const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -764,10 +792,14 @@ hb_status gemm(hb_mlp *m, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *
     const int zs = (K + kpc - 1) / kpc;
     if (N <= 32) {
         dim3 g((M + kBM - 1) / kBM, (N + 31) / 32, zs);
-        k_tc_gemm<32><<<g, 128, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kpc, n_store, mode, m->d_err);
+        PD_CUDA(cudaFuncSetAttribute(k_tc_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_gemm_smem(32)));
+        k_tc_gemm<32><<<g, 128, tc_gemm_smem(32), st>>>(A, lda, B, ldb, C, ldc, M, N, K, kpc, n_store, mode, m->d_err);
     } else {
         dim3 g((M + kBM - 1) / kBM, (N + 127) / 128, zs);
-        k_tc_gemm<128><<<g, 128, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kpc, n_store, mode, m->d_err);
+        PD_CUDA(cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc_gemm_smem(128)));
+        k_tc_gemm<128><<<g, 128, tc_gemm_smem(128), st>>>(A, lda, B, ldb, C, ldc, M, N, K, kpc, n_store, mode,
+                                                          m->d_err);
     }
     PD_CUDA(cudaGetLastError());
     return HB_OK;
