@@ -349,8 +349,19 @@ hb_status hubbard_batch_layout(hb_batch_handle b, uint64_t *offsets /* [n+1] */)
 /* y = H_k x for every instance k in one launch (row groups of all instances
  * form one work list); dt HB_F64, HB_F32 or HB_FX64. */
 hb_status hubbard_batch_apply(hb_batch_handle b, hb_dtype dt, const void *x, void *y, void *stream);
-/* Autotuner of the batched H·v (rows per group 1/2/4, threads 128/256/512);
- * keeps the fastest in the batch.  x and y are batch vectors (y overwritten). */
+/* Launch configuration of the batched H·v (the fields of hb_hv_config):
+ *   one kernel (split 0): rows_per_cta 1, 2 or 4 per item, threads_per_cta <= 512;
+ *   split form (split 1, fixed point only, every instance with a warp-blocked
+ *   table): a row pass (diagonal + spin-down hops, rows_per_cta 1 or 2) over all
+ *   instances, then the spin-up pass over column blocks (up_block columns,
+ *   up_threads <= 512 threads, up_rows rows per thread) of all instances.
+ * HB_ERR_INVALID_ARG for out-of-range fields or a split the batch cannot take. */
+hb_status hubbard_batch_get_config(hb_batch_handle b, hb_hv_config *cfg);
+hb_status hubbard_batch_set_config(hb_batch_handle b, const hb_hv_config *cfg);
+/* Autotuner of the batched H·v: the one-kernel form (rows per group 1/2/4,
+ * threads 128/256/512) and, for fixed point, the split form (row pass rows 1/2,
+ * threads 256/512, then seven spin-up shapes); keeps the fastest in the batch.
+ * x and y are batch vectors (y overwritten). */
 hb_status hubbard_batch_autotune(hb_batch_handle b, hb_dtype dt, const void *x, void *y, int32_t reps,
                                  hb_hv_config *best, void *stream);
 hb_status lanczos_batch_workspace_bytes(hb_batch_handle b, const hb_lanczos_opts *opts, uint64_t *bytes);

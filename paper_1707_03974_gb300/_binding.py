@@ -126,6 +126,8 @@ def load():
         "hubbard_batch_layout": (ctypes.c_int, [P, P]),
         "hubbard_batch_apply": (ctypes.c_int, [P, I32, P, P, P]),
         "hubbard_batch_autotune": (ctypes.c_int, [P, I32, P, P, I32, ctypes.POINTER(HvConfig), P]),
+        "hubbard_batch_get_config": (ctypes.c_int, [P, ctypes.POINTER(HvConfig)]),
+        "hubbard_batch_set_config": (ctypes.c_int, [P, ctypes.POINTER(HvConfig)]),
         "lanczos_batch_workspace_bytes": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), ctypes.POINTER(U64)]),
         "lanczos_batch_ground_state": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, U64, P, P, P]),
         "lanczos_batch_wait_selftest": (ctypes.c_int, [P, ctypes.POINTER(LanczosOpts), P, U64, ctypes.c_int32,
@@ -527,6 +529,19 @@ def hubbard_batch_apply(b: Batch, x, y=None, stream=None):
     _check(load().hubbard_batch_apply(b._b, _dtype_code(x), _ptr(x), _ptr(y), _stream_ptr(stream)),
            "hubbard_batch_apply")
     return y
+
+
+def hubbard_batch_get_config(b: Batch) -> dict:
+    c = HvConfig()
+    _check(load().hubbard_batch_get_config(b._b, ctypes.byref(c)), "hubbard_batch_get_config")
+    return c.as_dict()
+
+
+def hubbard_batch_set_config(b: Batch, rows_per_cta=0, threads_per_cta=0, split=0, up_block=0, up_threads=0,
+                             up_rows=0):
+    c = HvConfig(int(rows_per_cta), int(threads_per_cta), 1, 0.0, int(split), int(up_block), int(up_threads),
+                 int(up_rows))
+    _check(load().hubbard_batch_set_config(b._b, ctypes.byref(c)), "hubbard_batch_set_config")
 
 
 def hubbard_batch_autotune(b: Batch, x, y, reps: int = 3, stream=None) -> dict:

@@ -85,6 +85,76 @@ __global__ void __launch_bounds__(512) k_batch_hv(const Inst *__restrict__ inst,
     }
 }
 
+// ---- split form of the batched fixed-point H·v ----
+// Row pass: items (instance k, row group g of R rows), y = diag + spin-down hops
+// on the instance's warp-blocked table.  Spin-up pass: items (instance k,
+// column block j, row group g), column-block-major within an instance, y +=
+// spin-up hops; pairs of columns per thread where D_dn is even.
+template <int R, int NC>
+__global__ void __launch_bounds__(512) k_batch_row(const Inst *__restrict__ inst, const uint64_t *__restrict__ prefix,
+                                                   int n, const int *__restrict__ active, const int64_t *x,
+                                                   int64_t *y) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];
+    Inst &s_inst = *reinterpret_cast<Inst *>(s_inst_raw);
+    __shared__ int s_k;
+    const uint64_t total = prefix[n];
+    int cur = -1;
+    for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_k = find_inst(prefix, n, it);
+        __syncthreads();
+        const int k = s_k;
+        if (active && !active[k]) continue;  // uniform across the CTA
+        if (k != cur) {
+            copy_inst(&s_inst, inst + k);
+            __syncthreads();
+            hv_fx_load_diag(s_inst.fx, smem);
+            cur = k;
+        }
+        hv_fx_wb_group<R, NC>(s_inst.fx, x + s_inst.off, y + s_inst.off, it - prefix[k], smem);
+    }
+}
+
+// column block j and row group g of spin-up item `local` of an instance
+__device__ __forceinline__ void up_item_of(const FxArgs &a, uint64_t local, int RA, uint64_t *j, uint64_t *g) {
+    const uint64_t ng = (a.Du + RA - 1) / RA;
+    *j = local / ng;
+    *g = local - *j * ng;
+}
+
+template <int RR, int NC>
+__global__ void __launch_bounds__(512) k_batch_up(const Inst *__restrict__ inst, const uint64_t *__restrict__ up_prefix,
+                                                  int n, const int *__restrict__ active, const int64_t *x,
+                                                  int64_t *y, int W, int S) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];
+    Inst &s_inst = *reinterpret_cast<Inst *>(s_inst_raw);
+    __shared__ int s_k;
+    const uint64_t total = up_prefix[n];
+    int cur = -1;
+    for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_k = find_inst(up_prefix, n, it);
+        __syncthreads();
+        const int k = s_k;
+        if (active && !active[k]) continue;
+        if (k != cur) {
+            copy_inst(&s_inst, inst + k);
+            __syncthreads();
+            cur = k;
+        }
+        uint64_t j, g;
+        up_item_of(s_inst.fx, it - up_prefix[k], S * RR, &j, &g);
+        const int64_t *xk = x + s_inst.off;
+        int64_t *yk = y + s_inst.off;
+        if (s_inst.fx.Dd % 2 == 0)
+            hv_fx_up_item<RR, NC, true, 2>(s_inst.fx, xk, yk, j, g, W, S, smem);
+        else
+            hv_fx_up_item<RR, NC, true, 1>(s_inst.fx, xk, yk, j, g, W, S, smem);
+    }
+}
+
 // ---------------- batched Lanczos: one persistent kernel for all instances ----------------
 using pdx::block_sum128;
 using pdx::block_sum_d;
@@ -378,6 +448,8 @@ struct PState {
     GridSync *gs;
     unsigned long long limit_ns;
     int withhold;            // CTA that leaves before its first arrival (the wait self-test), -1: none
+    const uint64_t *up_prefix;  // split form: prefix sums of the spin-up items
+    int up_W, up_S;             // split form: spin-up columns per block and row slots (up_W * up_S threads)
 };
 
 // Store hook of the H·v (fixed point): w = H v - beta_prev vprev and the exact
@@ -450,19 +522,25 @@ __device__ __forceinline__ int inst_at(const Inst *inst, int n, uint64_t e) {
 // check_every steps, the tridiagonal solve of each instance by the CTA that
 // holds its first element; barrier.  With fixed-point vectors both reductions
 // are exact 128-bit sums (converted to float64 once, through double-double).
-template <int R, int NC, bool FX>
+template <int R, int NC, bool FX, bool SPLIT>
 __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) k_batch_lanczos(PState p) {
+    static_assert(FX || !SPLIT, "the split form is fixed point only");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];  // filled by copy_inst, no constructor
     Inst &s_inst = *reinterpret_cast<Inst *>(s_inst_raw);
     __shared__ int s_k;
     __shared__ double s_ab[2];
     __shared__ uint64_t s_prefix[kSmemPrefix + 1];  // item prefix sums, when the batch is small enough
+    __shared__ uint64_t s_up_prefix[SPLIT ? kSmemPrefix + 1 : 1];
     const bool pre_smem = p.n <= kSmemPrefix;
     if (pre_smem)
-        for (int k = threadIdx.x; k <= p.n; k += blockDim.x) s_prefix[k] = p.prefix[k];
+        for (int k = threadIdx.x; k <= p.n; k += blockDim.x) {
+            s_prefix[k] = p.prefix[k];
+            if (SPLIT) s_up_prefix[k] = p.up_prefix[k];
+        }
     __syncthreads();
     const uint64_t *prefix = pre_smem ? s_prefix : p.prefix;
+    const uint64_t *up_prefix = SPLIT ? (pre_smem ? s_up_prefix : p.up_prefix) : nullptr;
     using T = typename std::conditional<FX, int64_t, double>::type;
     const unsigned G = gridDim.x;
     const uint64_t n_items = p.prefix[p.n];
@@ -495,38 +573,78 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
                 epi.swv = 0.0;
             }
         };
-        for (uint64_t it = blockIdx.x; it < n_items; it += G) {
+        // instance k becomes the CTA's current one: descriptor, diagonal table, hook pointers
+        auto enter = [&](int k, bool diag) {
             __syncthreads();
-            if (threadIdx.x == 0) s_k = find_inst(prefix, p.n, it);
+            copy_inst(&s_inst, p.inst + k);
             __syncthreads();
-            const int k = s_k;
-            if (!p.active[k]) continue;  // uniform across the CTA
-            if (k != cur) {
-                if (cur >= 0) flush(cur);
-                __syncthreads();
-                copy_inst(&s_inst, p.inst + k);
-                __syncthreads();
-                if (FX) hv_fx_load_diag(s_inst.fx, smem);
-                cur = k;
-                const uint64_t off = s_inst.off;
-                epi.w = V + iw * p.stride + off;
-                epi.vprev = V + ip * p.stride + off;
-                epi.has_prev = j > 0;
-                const double bp = j > 0 ? p.beta[(uint64_t)k * p.maxit1 + j - 1] : 0.0;
-                if constexpr (FX) {
-                    const FxCoef c = fx_coef_dev(bp);
-                    epi.Kb = c.K;
-                    epi.Gb = c.G;
-                } else {
-                    epi.bprev = bp;
-                }
+            if (diag) hv_fx_load_diag(s_inst.fx, smem);
+            cur = k;
+            const uint64_t off = s_inst.off;
+            epi.w = V + iw * p.stride + off;
+            epi.vprev = V + ip * p.stride + off;
+            epi.has_prev = j > 0;
+            const double bp = j > 0 ? p.beta[(uint64_t)k * p.maxit1 + j - 1] : 0.0;
+            if constexpr (FX) {
+                const FxCoef c = fx_coef_dev(bp);
+                epi.Kb = c.K;
+                epi.Gb = c.G;
+            } else {
+                epi.bprev = bp;
             }
-            const uint64_t g = it - prefix[k];
-            const T *v = V + iv * p.stride + s_inst.off;
-            if constexpr (FX)
-                hv_fx_group<R, NC, true, true, FxStepEpi>(s_inst.fx, v, nullptr, g, smem, &epi);
-            else
-                hv_group<R, double, true, true, F64StepEpi>(s_inst.f64, v, nullptr, g, smem, &epi);
+        };
+        if constexpr (SPLIT) {
+            // row pass of every active instance: w = diag + spin-down hops
+            for (uint64_t it = blockIdx.x; it < n_items; it += G) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_k = find_inst(prefix, p.n, it);
+                __syncthreads();
+                const int k = s_k;
+                if (!p.active[k]) continue;
+                if (k != cur) enter(k, true);
+                hv_fx_wb_group<R, NC>(s_inst.fx, V + iv * p.stride + s_inst.off, V + iw * p.stride + s_inst.off,
+                                      it - prefix[k], smem);
+            }
+            if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
+            // spin-up pass; its hook adds - beta vprev and accumulates <w, v>
+            cur = -1;
+            const uint64_t n_up = up_prefix[p.n];
+            for (uint64_t it = blockIdx.x; it < n_up; it += G) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_k = find_inst(up_prefix, p.n, it);
+                __syncthreads();
+                const int k = s_k;
+                if (!p.active[k]) continue;
+                if (k != cur) {
+                    if (cur >= 0) flush(cur);
+                    enter(k, false);
+                }
+                uint64_t jb, g;
+                up_item_of(s_inst.fx, it - up_prefix[k], p.up_S * 2, &jb, &g);
+                const int64_t *v = V + iv * p.stride + s_inst.off;
+                if (s_inst.fx.Dd % 2 == 0)
+                    hv_fx_up_item<2, NC, true, 2, FxStepEpi>(s_inst.fx, v, epi.w, jb, g, p.up_W, p.up_S, smem, &epi);
+                else
+                    hv_fx_up_item<2, NC, true, 1, FxStepEpi>(s_inst.fx, v, epi.w, jb, g, p.up_W, p.up_S, smem, &epi);
+            }
+        } else {
+            for (uint64_t it = blockIdx.x; it < n_items; it += G) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_k = find_inst(prefix, p.n, it);
+                __syncthreads();
+                const int k = s_k;
+                if (!p.active[k]) continue;  // uniform across the CTA
+                if (k != cur) {
+                    if (cur >= 0) flush(cur);
+                    enter(k, FX);
+                }
+                const uint64_t g = it - prefix[k];
+                const T *v = V + iv * p.stride + s_inst.off;
+                if constexpr (FX)
+                    hv_fx_group<R, NC, true, true, FxStepEpi>(s_inst.fx, v, nullptr, g, smem, &epi);
+                else
+                    hv_group<R, double, true, true, F64StepEpi>(s_inst.f64, v, nullptr, g, smem, &epi);
+            }
         }
         if (cur >= 0) flush(cur);
         if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
@@ -678,6 +796,13 @@ struct hb_batch {
     int max_classes = 1;
     int rows = 2, threads = 256;  // batched H·v launch configuration
     hb_dtype desc_dtype = HB_F64;
+    // split form (fixed point): row pass on each instance's warp-blocked table, then the
+    // column-blocked spin-up pass; items of the spin-up pass: prefix over instances
+    int split = 0;
+    bool split_ok = false;  // every instance has a warp-blocked table and D < 2^32
+    int up_W = 128, up_S = 2, up_RR = 2, up_threads = 256;
+    uint64_t *d_up_prefix = nullptr;
+    std::vector<uint64_t> up_items;
 };
 
 namespace {
@@ -742,11 +867,32 @@ hb_status build_desc(hb_batch *b, int R) {
                 x.Gc[c] = cls[c].G;
             }
         }
+        if (h->dn.wb_ok) {
+            x.wb_perm = h->dn.wb_perm;
+            x.wb_str = h->dn.wb_str;
+            x.wb_base = h->dn.wb_base;
+            x.wb_ent = h->dn.wb_ent;
+            x.wb_caps = h->dn.wb_caps;
+            x.wb_nblk = h->dn.wb_nblk;
+        }
         prefix[k + 1] = prefix[k] + (h->D_up + R - 1) / R;
+    }
+    // spin-up pass items: (column block, row group) of every instance, column-block-major
+    b->split_ok = true;
+    std::vector<uint64_t> up(b->n + 1, 0);
+    const uint64_t RA = (uint64_t)b->up_S * b->up_RR;
+    for (int k = 0; k < b->n; ++k) {
+        hb_handle h = b->h[k];
+        b->split_ok = b->split_ok && h->fx_ok && h->dn.wb_ok && h->D < (1ull << 32);
+        const uint64_t V = h->D_dn % 2 == 0 ? 2 : 1;
+        const uint64_t cols = (uint64_t)b->up_W * V;
+        up[k + 1] = up[k] + (h->D_dn + cols - 1) / cols * ((h->D_up + RA - 1) / RA);
     }
     PD_CUDA(cudaMemcpy(b->d_inst, host.data(), sizeof(Inst) * b->n, cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(b->d_prefix, prefix.data(), sizeof(uint64_t) * (b->n + 1), cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(b->d_up_prefix, up.data(), sizeof(uint64_t) * (b->n + 1), cudaMemcpyHostToDevice));
     b->items = prefix;
+    b->up_items = up;
     return HB_OK;
 }
 
@@ -786,7 +932,69 @@ hb_status batch_hv_r(hb_batch *b, hb_dtype dt, const void *x, void *y, const int
     }
 }
 
+size_t batch_row_smem(const hb_batch *b, int R) {
+    size_t m = 0;
+    for (hb_handle h : b->h) m = std::max(m, hv_fx_wb_smem_bytes(R, h->D_dn));
+    return m;
+}
+size_t batch_up_smem(const hb_batch *b) {
+    size_t m = 0;
+    for (hb_handle h : b->h) m = std::max(m, hv_fx_up_smem_bytes<true>(b->up_S * b->up_RR, h->up.zmax));
+    return m;
+}
+
+template <int R, int NC>
+hb_status launch_batch_row(hb_batch *b, const int64_t *x, int64_t *y, const int *active, cudaStream_t st) {
+    auto kern = k_batch_row<R, NC>;
+    const size_t smem = batch_row_smem(b, R);
+    PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->threads, smem));
+    if (per_sm < 1) return HB_ERR_NO_MEMORY;
+    const uint64_t grid = std::min<uint64_t>(b->items[b->n], (uint64_t)per_sm * b->sm_count);
+    kern<<<(unsigned)std::max<uint64_t>(grid, 1), b->threads, smem, st>>>(b->d_inst, b->d_prefix, b->n, active, x, y);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+template <int RR, int NC>
+hb_status launch_batch_up(hb_batch *b, const int64_t *x, int64_t *y, const int *active, cudaStream_t st) {
+    auto kern = k_batch_up<RR, NC>;
+    const size_t smem = batch_up_smem(b);
+    const int threads = b->up_W * b->up_S;
+    PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) return HB_ERR_NO_MEMORY;
+    const uint64_t grid = std::min<uint64_t>(b->up_items[b->n], (uint64_t)per_sm * b->sm_count);
+    kern<<<(unsigned)std::max<uint64_t>(grid, 1), threads, smem, st>>>(b->d_inst, b->d_up_prefix, b->n, active, x, y,
+                                                                       b->up_W, b->up_S);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+template <int NC>
+hb_status batch_hv_split_nc(hb_batch *b, const int64_t *x, int64_t *y, const int *active, cudaStream_t st) {
+    hb_status s = b->rows == 1 ? launch_batch_row<1, NC>(b, x, y, active, st) : launch_batch_row<2, NC>(b, x, y, active, st);
+    if (s != HB_OK) return s;
+    if (b->up_RR == 4) return launch_batch_up<4, NC>(b, x, y, active, st);
+    if (b->up_RR == 2) return launch_batch_up<2, NC>(b, x, y, active, st);
+    return launch_batch_up<1, NC>(b, x, y, active, st);
+}
+
+hb_status batch_hv_split(hb_batch *b, const void *x, void *y, const int *active, cudaStream_t st) {
+    const int64_t *xi = static_cast<const int64_t *>(x);
+    int64_t *yi = static_cast<int64_t *>(y);
+    switch (b->max_classes) {
+        case 1: return batch_hv_split_nc<1>(b, xi, yi, active, st);
+        case 2: return batch_hv_split_nc<2>(b, xi, yi, active, st);
+        case 3: return batch_hv_split_nc<3>(b, xi, yi, active, st);
+        default: return batch_hv_split_nc<4>(b, xi, yi, active, st);
+    }
+}
+
 hb_status batch_hv(hb_batch *b, hb_dtype dt, const void *x, void *y, const int *active, cudaStream_t st) {
+    if (dt == HB_FX64 && b->split && b->split_ok) return batch_hv_split(b, x, y, active, st);
     if (b->rows == 4) return batch_hv_r<4>(b, dt, x, y, active, st);
     if (b->rows == 1) return batch_hv_r<1>(b, dt, x, y, active, st);
     return batch_hv_r<2>(b, dt, x, y, active, st);
@@ -825,7 +1033,8 @@ hb_status hubbard_batch_create(int n, const hb_handle *handles, hb_batch_handle 
     b->sm_count = handles[0]->sm_count;
     if (cudaMalloc(&b->d_inst, sizeof(Inst) * n) != cudaSuccess ||
         cudaMalloc(&b->d_prefix, sizeof(uint64_t) * (n + 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_all_active, sizeof(int) * n) != cudaSuccess) {
+        cudaMalloc(&b->d_all_active, sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_up_prefix, sizeof(uint64_t) * (n + 1)) != cudaSuccess) {
         hubbard_batch_destroy(b);
         return HB_ERR_NO_MEMORY;
     }
@@ -840,6 +1049,7 @@ hb_status hubbard_batch_destroy(hb_batch_handle b) {
     cudaFree(b->d_inst);
     cudaFree(b->d_prefix);
     cudaFree(b->d_all_active);
+    cudaFree(b->d_up_prefix);
     delete b;
     return HB_OK;
 }
@@ -860,6 +1070,40 @@ hb_status hubbard_batch_apply(hb_batch_handle b, hb_dtype dt, const void *x, voi
     return batch_hv(b, dt, x, y, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
 
+hb_status hubbard_batch_get_config(hb_batch_handle b, hb_hv_config *cfg) {
+    if (!b || !cfg) return HB_ERR_INVALID_ARG;
+    cfg->rows_per_cta = b->rows;
+    cfg->threads_per_cta = b->threads;
+    cfg->visit_order = 1;
+    cfg->ms = 0.f;
+    cfg->split = b->split;
+    cfg->up_block = b->split ? b->up_W : 0;
+    cfg->up_threads = b->split ? b->up_W * b->up_S : 0;
+    cfg->up_rows = b->split ? b->up_RR : 0;
+    return HB_OK;
+}
+
+hb_status hubbard_batch_set_config(hb_batch_handle b, const hb_hv_config *c) {
+    if (!b || !c) return HB_ERR_INVALID_ARG;
+    const int R = c->rows_per_cta ? c->rows_per_cta : 2, T = c->threads_per_cta ? c->threads_per_cta : 256;
+    if ((R != 1 && R != 2 && R != 4) || T < 32 || T > 512 || T % 32 || (c->split != 0 && c->split != 1))
+        return HB_ERR_INVALID_ARG;
+    int W = b->up_W, S = b->up_S, RR = b->up_RR;
+    if (c->split) {
+        W = c->up_block ? c->up_block : 128;
+        const int UT = c->up_threads ? c->up_threads : 256;
+        RR = c->up_rows ? c->up_rows : 2;
+        if (W < 32 || W % 32 || UT % W || UT > 512 || (RR != 1 && RR != 2 && RR != 4) || R == 4)
+            return HB_ERR_INVALID_ARG;
+        S = UT / W;
+    }
+    hb_status s = batch_prepare(b);  // builds the tables, so that split_ok is known
+    if (s != HB_OK) return s;
+    if (c->split && !b->split_ok) return HB_ERR_INVALID_ARG;
+    b->rows = R, b->threads = T, b->split = c->split, b->up_W = W, b->up_S = S, b->up_RR = RR;
+    return batch_prepare(b);
+}
+
 hb_status hubbard_batch_autotune(hb_batch_handle b, hb_dtype dt, const void *x, void *y, int32_t reps,
                                  hb_hv_config *best, void *stream) {
     if (!b || !x || !y || reps < 1) return HB_ERR_INVALID_ARG;
@@ -867,44 +1111,72 @@ hb_status hubbard_batch_autotune(hb_batch_handle b, hb_dtype dt, const void *x, 
     cudaEvent_t e0, e1;
     PD_CUDA(cudaEventCreate(&e0));
     PD_CUDA(cudaEventCreate(&e1));
-    int bestR = b->rows, bestT = b->threads;
+    // average time of reps batched applications under the batch's current configuration
+    auto time_cfg = [&](float *ms) -> hb_status {
+        hb_status s = batch_prepare(b);
+        if (s != HB_OK || (s = batch_hv(b, dt, x, y, nullptr, st)) != HB_OK) return s;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps && s == HB_OK; ++k) s = batch_hv(b, dt, x, y, nullptr, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        *ms = t / reps;
+        return s;
+    };
+    struct Cfg {
+        int split, R, T, W, S, RR;
+    };
+    Cfg bestc = {0, b->rows, b->threads, b->up_W, b->up_S, b->up_RR};
     float best_ms = 3.4e38f;
     hb_status s = HB_OK;
-    for (int R : {1, 2, 4}) {
-        for (int T : {128, 256, 512}) {
-            b->rows = R;
-            b->threads = T;
-            if ((s = batch_prepare(b)) != HB_OK) break;
-            if ((s = batch_hv(b, dt, x, y, nullptr, st)) != HB_OK) break;
-            cudaEventRecord(e0, st);
-            for (int k = 0; k < reps && s == HB_OK; ++k) s = batch_hv(b, dt, x, y, nullptr, st);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= reps;
-            if (s == HB_OK && ms < best_ms) {
-                best_ms = ms;
-                bestR = R;
-                bestT = T;
+    auto apply = [&](const Cfg &c) {
+        b->split = c.split, b->rows = c.R, b->threads = c.T, b->up_W = c.W, b->up_S = c.S, b->up_RR = c.RR;
+    };
+    auto consider = [&](const Cfg &c) {
+        if (s != HB_OK) return;
+        apply(c);
+        float ms = 0.f;
+        s = time_cfg(&ms);
+        if (s == HB_OK && ms < best_ms) best_ms = ms, bestc = c;
+    };
+    // one kernel over all terms
+    for (int R : {1, 2, 4})
+        for (int T : {128, 256, 512}) consider({0, R, T, b->up_W, b->up_S, b->up_RR});
+    // split form (fixed point, every instance with a warp-blocked table): the row pass first, under
+    // a default spin-up shape, then the spin-up shape under the best row pass
+    apply(bestc);
+    if (s == HB_OK && dt == HB_FX64 && batch_prepare(b) == HB_OK && b->split_ok) {
+        Cfg row_best = {1, 2, 256, 128, 2, 2};
+        float row_ms = 3.4e38f;
+        for (int R : {1, 2})
+            for (int T : {256, 512}) {
+                if (s != HB_OK) break;
+                const Cfg c = {1, R, T, 128, 2, 2};
+                apply(c);
+                float ms = 0.f;
+                s = time_cfg(&ms);
+                if (s == HB_OK && ms < row_ms) row_ms = ms, row_best = c;
+                if (s == HB_OK && ms < best_ms) best_ms = ms, bestc = c;
             }
-        }
-        if (s != HB_OK) break;
+        const int shapes[][3] = {{32, 8, 2}, {64, 4, 2}, {64, 8, 1}, {128, 4, 1}, {128, 2, 4}, {256, 2, 2}, {512, 1, 2}};
+        for (const auto &sh : shapes) consider({1, row_best.R, row_best.T, sh[0], sh[1], sh[2]});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->rows = bestR;
-    b->threads = bestT;
+    apply(bestc);
     hb_status s2 = batch_prepare(b);
     if (s != HB_OK) return s;
     if (s2 != HB_OK) return s2;
     if (best) {
-        best->rows_per_cta = bestR;
-        best->threads_per_cta = bestT;
+        best->rows_per_cta = bestc.R;
+        best->threads_per_cta = bestc.T;
         best->visit_order = 1;
         best->ms = best_ms;
-        best->split = 0;  // the batched H·v is always one kernel
-        best->up_block = best->up_threads = best->up_rows = 0;
+        best->split = bestc.split;
+        best->up_block = bestc.split ? bestc.W : 0;
+        best->up_threads = bestc.split ? bestc.W * bestc.S : 0;
+        best->up_rows = bestc.split ? bestc.RR : 0;
     }
     return HB_OK;
 }
@@ -937,23 +1209,23 @@ static BatchWs batch_layout_ws(hb_batch_handle b, const hb_lanczos_opts *o) {
     return L;
 }
 
-template <int R, int NC, bool FX>
+template <int R, int NC, bool FX, bool SPLIT>
 hb_status pick_persistent(hb_batch *b, size_t smem, void **kern, int *per_sm) {
-    auto k = k_batch_lanczos<R, NC, FX>;
+    auto k = k_batch_lanczos<R, NC, FX, SPLIT>;
     PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kPThreads, smem));
     *kern = reinterpret_cast<void *>(k);
     return HB_OK;
 }
 
-template <int R>
+template <int R, bool SPLIT>
 hb_status pick_persistent_r(hb_batch *b, bool fx, size_t smem, void **kern, int *per_sm) {
-    if (!fx) return pick_persistent<R, 1, false>(b, smem, kern, per_sm);
+    if (!fx) return pick_persistent<R, 1, false, false>(b, smem, kern, per_sm);
     switch (b->max_classes) {
-        case 1: return pick_persistent<R, 1, true>(b, smem, kern, per_sm);
-        case 2: return pick_persistent<R, 2, true>(b, smem, kern, per_sm);
-        case 3: return pick_persistent<R, 3, true>(b, smem, kern, per_sm);
-        default: return pick_persistent<R, 4, true>(b, smem, kern, per_sm);
+        case 1: return pick_persistent<R, 1, true, SPLIT>(b, smem, kern, per_sm);
+        case 2: return pick_persistent<R, 2, true, SPLIT>(b, smem, kern, per_sm);
+        case 3: return pick_persistent<R, 3, true, SPLIT>(b, smem, kern, per_sm);
+        default: return pick_persistent<R, 4, true, SPLIT>(b, smem, kern, per_sm);
     }
 }
 
@@ -991,17 +1263,32 @@ hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, 
     int coop = 0;
     PD_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device));
     if (!coop) return HB_ERR_CUDA;
-    const int R = b->rows == 1 ? 1 : b->rows == 4 ? 4 : 2;  // rows per item: the batched H·v's tuned row count
     hb_status st = batch_prepare(b);
-    if (st == HB_OK && R != b->rows) st = build_desc(b, R);  // items of R rows (batch_prepare rebuilds for apply)
     if (st != HB_OK) return st;
-    const hb_dtype dt = FX ? HB_FX64 : HB_F64;
-    const size_t smem = batch_smem(b, R, dt);
+    // the batched H·v's tuned form: the split form (fixed point, warp-blocked tables) or one kernel
+    const bool split = FX && b->split && b->split_ok;
+    const int R = split ? (b->rows == 1 ? 1 : 2) : (b->rows == 1 ? 1 : b->rows == 4 ? 4 : 2);
+    // the spin-up shape of the persistent kernel: kPThreads threads, two rows per thread
+    const int saved_W = b->up_W, saved_S = b->up_S, saved_RR = b->up_RR;
+    if (split) {
+        b->up_W = (b->up_W * b->up_S == kPThreads && b->up_RR == 2) ? b->up_W : 128;
+        b->up_S = kPThreads / b->up_W;
+        b->up_RR = 2;
+    }
+    st = build_desc(b, R);  // items of R rows and the spin-up items of that shape (batch_prepare rebuilds for apply)
+    const int up_W = b->up_W, up_S = b->up_S;
+    const size_t smem = split ? std::max(batch_row_smem(b, R), batch_up_smem(b)) : batch_smem(b, R, FX ? HB_FX64 : HB_F64);
+    b->up_W = saved_W, b->up_S = saved_S, b->up_RR = saved_RR;
+    if (st != HB_OK) return st;
     void *kern = nullptr;
     int per_sm = 0;
-    st = R == 1   ? pick_persistent_r<1>(b, FX, smem, &kern, &per_sm)
-         : R == 4 ? pick_persistent_r<4>(b, FX, smem, &kern, &per_sm)
-                  : pick_persistent_r<2>(b, FX, smem, &kern, &per_sm);
+    if (split)
+        st = R == 1 ? pick_persistent_r<1, true>(b, FX, smem, &kern, &per_sm)
+                    : pick_persistent_r<2, true>(b, FX, smem, &kern, &per_sm);
+    else
+        st = R == 1   ? pick_persistent_r<1, false>(b, FX, smem, &kern, &per_sm)
+             : R == 4 ? pick_persistent_r<4, false>(b, FX, smem, &kern, &per_sm)
+                      : pick_persistent_r<2, false>(b, FX, smem, &kern, &per_sm);
     if (st != HB_OK) return st;
     if (per_sm < 1) return HB_ERR_NO_MEMORY;
     const unsigned grid = (unsigned)std::min(per_sm * b->sm_count, L.gmax);
@@ -1034,6 +1321,9 @@ hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, 
     p.gs = reinterpret_cast<GridSync *>(ws + L.sync);
     p.limit_ns = limit_ns;
     p.withhold = withhold;
+    p.up_prefix = b->d_up_prefix;
+    p.up_W = up_W;
+    p.up_S = up_S;
 
     cudaStream_t cs;
     PD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

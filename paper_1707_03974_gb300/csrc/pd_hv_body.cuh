@@ -508,10 +508,13 @@ __device__ __forceinline__ void up_segment_fx(const int64_t *__restrict__ x, con
         if (kend - k >= 1) up_batch_fx<OFF, 1, V>(x, uo, k, d, acc), k += 1;
 }
 
-template <int RR, int NC, bool IDX32, int V>
+// Epi: optional hook for the final value y_row + up of each element (the batched
+// Lanczos step fuses its first vector pass there); with the default (void) the
+// sum is stored back to y.
+template <int RR, int NC, bool IDX32, int V, class Epi = void>
 __device__ __forceinline__ void hv_fx_up_item(const FxArgs &a, const int64_t *__restrict__ x,
                                               int64_t *__restrict__ y, uint64_t j, uint64_t g, int W, int S,
-                                              unsigned char *smem) {
+                                              unsigned char *smem, Epi *epi = nullptr) {
     using OFF = typename std::conditional<IDX32, uint32_t, uint64_t>::type;
     const uint64_t Dd = a.Dd;
     const int RA = S * RR;
@@ -555,7 +558,12 @@ __device__ __forceinline__ void hv_fx_up_item(const FxArgs &a, const int64_t *__
         Pack<int64_t, V> yv = *yp;
 #pragma unroll
         for (int v = 0; v < V; ++v) yv.v[v] = (int64_t)((uint64_t)yv.v[v] + add[v]);
-        *yp = yv;
+        if constexpr (std::is_void<Epi>::value) {
+            *yp = yv;
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) epi->store(u * Dd + d + v, yv.v[v], x[u * Dd + d + v]);
+        }
     }
 }
 

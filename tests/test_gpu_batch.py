@@ -44,6 +44,22 @@ def test_batch_apply_equals_single_applies(batch, dtype_name):
         assert torch.equal(b.view(y, k), ref), k
 
 
+@pytest.mark.parametrize("shape", [(64, 4, 2), (128, 2, 2), (32, 8, 1), (256, 1, 4)])
+def test_batch_split_form_equals_single_applies(batch, shape):
+    """The split batched H·v (row pass on each instance's warp-blocked table, then the
+    column-blocked spin-up pass) gives the same integers as each instance's own H·v."""
+    torch, pd, insts, hs, b = batch
+    x = torch.zeros(b.total, dtype=torch.int64, device="cuda")
+    for k, h in enumerate(hs):
+        v = torch.from_numpy(start_vector(300 + k, h.D)).cuda()
+        b.view(x, k).copy_(pd.hubbard_convert(h, v, torch.int64))
+    pd.hubbard_batch_set_config(b, split=1, rows_per_cta=2, threads_per_cta=256, up_block=shape[0],
+                                up_threads=shape[0] * shape[1], up_rows=shape[2])
+    y = pd.hubbard_batch_apply(b, x)
+    for k, h in enumerate(hs):
+        assert torch.equal(b.view(y, k), pd.hubbard_apply(h, b.view(x, k).contiguous())), k
+
+
 def test_batch_autotune_keeps_results(batch):
     torch, pd, insts, hs, b = batch
     x = torch.zeros(b.total, dtype=torch.float64, device="cuda")
@@ -61,6 +77,24 @@ def test_batch_lanczos_matches_oracle(batch, dtype_name):
     torch, pd, insts, hs, b = batch
     E0, infos, status = pd.lanczos_batch_ground_state(b, maxit=1500, tol=1e-10, dtype=getattr(torch, dtype_name),
                                                       seed=0, check_every=10)
+    assert status == "HB_OK"
+    g = gold()
+    for k in range(64):
+        assert infos[k]["converged"]
+        assert abs(E0[k] - g[k]["E0"]) <= 1e-10 * max(1.0, abs(g[k]["E0"])), (k, E0[k], g[k]["E0"])
+
+
+def test_batch_lanczos_split_form_matches_oracle(batch):
+    """The persistent batched solve with the split H·v (row-pass phase, grid barrier, spin-up phase
+    whose hook forms w = H v - beta vprev and <w, v>): all 64 E0 within 1e-10 of the oracle."""
+    torch, pd, insts, hs, b = batch
+    pd.hubbard_batch_set_config(b, split=1, rows_per_cta=2, threads_per_cta=256, up_block=128, up_threads=256,
+                                up_rows=2)
+    try:
+        E0, infos, status = pd.lanczos_batch_ground_state(b, maxit=1500, tol=1e-10, dtype=torch.int64, seed=0,
+                                                          check_every=10)
+    finally:
+        pd.hubbard_batch_set_config(b, split=0, rows_per_cta=2, threads_per_cta=256)
     assert status == "HB_OK"
     g = gold()
     for k in range(64):
