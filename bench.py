@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="hubbard4x4_half",
-                   choices=sorted(WORKLOADS) + ["batch64", "learned4x4", "start4x4", "green4x4", "ceilings"])
+                   choices=sorted(WORKLOADS) + ["batch64", "learned4x4", "start4x4", "green4x4", "ceilings", "tcgemm"])
     p.add_argument("--dtype", default="fx64", choices=["f64", "fx64", "f32"],
                    help="Krylov vector type: fixed-point int64 (default, float64-grade accuracy without the "
                         "float64 pipe), float64 (float64 FMAs), float32")
@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the library's default H·v launch configuration")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the other configurations (batch, momentum sector, 18-site, learned start)")
     p.add_argument("--basis", default="hubbard4x4_half", choices=sorted(WORKLOADS),
                    help="basis of the start4x4 workload (the start vector is built over all of it)")
     p.add_argument("--hv-config", default=None,
@@ -373,6 +375,14 @@ def run_ours(args, world, rank, local):
         solve = precision_e0(pd, h, torch)
     del V
     h.close()
+    torch.cuda.empty_cache()
+    # the other configurations of the method, measured on rank 0 after the timed steps
+    extra = {}
+    if args.workload == "hubbard4x4_half" and rank == 0 and not args.no_solve and not args.no_extra:
+        extra["batch64"] = measure_batch64(pd, torch, wl, 10, 3, torch.int64)
+        extra["kspace4x4_K00"] = measure_kspace(pd, torch)
+        extra["tilted18_f32"] = measure_tilted18_f32(pd, torch, wl)
+        extra["learned4x4"] = measure_learned_quick(pd, torch, wl)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -422,6 +432,8 @@ def run_ours(args, world, rank, local):
         out["plain_f64_step"] = plain
     if solve:
         out["time_to_E0"] = solve
+    if extra:
+        out["other_workloads"] = extra
     if not args.no_cpu and args.workload == "hubbard4x4_half":
         out["cpu_baseline"] = cpu_baseline(sample_rows=20000)
     print(json.dumps(out))
@@ -645,18 +657,135 @@ def run_reference(args, world, rank):
     return out
 
 
-def run_batch(args, world, rank, local):
-    """64 independent 12-site problems solved together (batched H·v + graph-replayed Lanczos)."""
-    import torch
-    torch.cuda.set_device(local)
-    from paper_1707_03974_gb300.build import build
-    build()
-    import paper_1707_03974_gb300 as pd
-    import workloads as wl
+def measure_kspace(pd, torch, steps: int = 10):
+    """The K = (0,0) momentum sector of the 4x4 t-t' cluster (Sec. IV A, Eq. 4) in fixed point: H·v and
+    Lanczos step times, the H·v against HBM (16 B per sector state), and the time to E0 at 1e-10."""
+    h = pd.Handle.momentum(4, 4, 1.0, -0.3, 8.0, 8, 8, 0, 0)
+    D = h.D
+    V = [torch.zeros(D, dtype=torch.int64, device="cuda") for _ in range(3)]
+    x0 = torch.empty(D, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    V[0].copy_(pd.hubbard_convert(h, x0 / x0.norm(), torch.int64))
+    del x0
+    a = torch.zeros(steps + 4, dtype=torch.float64, device="cuda")
+    bt = torch.zeros(steps + 4, dtype=torch.float64, device="cuda")
+    scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device="cuda")
+    ev = []
+    for j in range(steps + 3):
+        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) if j >= 3 else (None, None)
+        if j >= 3:
+            e[0].record()
+            e[1].record()
+            ev.append(e)
+        pd.lanczos_step(h, V[j % 3], V[(j - 1) % 3] if j else None, V[(j + 1) % 3], bt[j - 1:j] if j else None,
+                        a[j:j + 1], bt[j:j + 1], scratch, e[0], e[1])
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for j in range(3, steps + 3):
+        pd.lanczos_step(h, V[j % 3], V[(j - 1) % 3], V[(j + 1) % 3], bt[j - 1:j], a[j:j + 1], bt[j:j + 1], scratch)
+    t1.record()
+    torch.cuda.synchronize()
+    hv_ms = statistics.mean(x.elapsed_time(y) for x, y in ev)
+    step_ms = t0.elapsed_time(t1) / steps
+    del V
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    r = pd.lanczos_ground_state(h, maxit=3000, tol=1e-10, seed=0, dtype=torch.int64, raise_on_error=False)
+    torch.cuda.synchronize()
+    e0_s = time.perf_counter() - t
+    peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    gbs = 16 * D / (hv_ms * 1e-3) / 1e9
+    h.close()
+    return {"workload": "hubbard_4x4_tp-0.3_U8_half_filling_momentum_K00", "D": D, "hv_ms": round(hv_ms, 4),
+            "step_ms": round(step_ms, 4), "hv_gstates_per_s": round(D / (hv_ms * 1e-3) / 1e9, 3),
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs / peak, 4), "kernel": "k_k_hv_rows<int64>", "bytes_per_state": 16},
+            "time_to_E0_fx64": {"seconds": round(e0_s, 4), "iterations": r.iterations, "E0": r.E0,
+                                "converged": r.converged}}
+
+
+def measure_tilted18_f32(pd, torch, wl, steps: int = 5):
+    """The 18-site tilted cluster (U = 6, (9,9), D = 2,363,904,400) with float32 vectors and float64
+    scalars: one Lanczos step and its H·v on the autotuned launch configuration."""
+    cl = wl.tilted_18()
+    h = pd.Handle(cl.L, cl.bonds, cl.t, 6.0, 9, 9)
+    D = h.D
+    V = [torch.zeros(D, dtype=torch.float32, device="cuda") for _ in range(3)]
+    V[0].uniform_(-1.0, 1.0)
+    V[0] /= V[0].norm()
+    pd.hubbard_autotune(h, V[0], V[1], reps=1)
+    a = torch.zeros(steps + 4, dtype=torch.float64, device="cuda")
+    bt = torch.zeros(steps + 4, dtype=torch.float64, device="cuda")
+    scratch = torch.empty(pd.lanczos_step_scratch_bytes(h), dtype=torch.uint8, device="cuda")
+    ev = []
+    for j in range(steps + 2):
+        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) if j >= 2 else (None, None)
+        if j >= 2:
+            e[0].record()
+            e[1].record()
+            ev.append(e)
+        pd.lanczos_step(h, V[j % 3], V[(j - 1) % 3] if j else None, V[(j + 1) % 3], bt[j - 1:j] if j else None,
+                        a[j:j + 1], bt[j:j + 1], scratch, e[0], e[1])
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for j in range(2, steps + 2):
+        pd.lanczos_step(h, V[j % 3], V[(j - 1) % 3], V[(j + 1) % 3], bt[j - 1:j], a[j:j + 1], bt[j:j + 1], scratch)
+    t1.record()
+    torch.cuda.synchronize()
+    hv_ms = statistics.mean(x.elapsed_time(y) for x, y in ev)
+    step_ms = t0.elapsed_time(t1) / steps
+    peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    gbs = 8 * D / (hv_ms * 1e-3) / 1e9
+    del V
+    h.close()
+    torch.cuda.empty_cache()
+    return {"workload": "hubbard_18site_tilted_U6_half_filling", "D": D, "vector_dtype": "f32",
+            "step_ms": round(step_ms, 3), "hv_ms": round(hv_ms, 3), "value_gstates_per_s": round(D / (step_ms * 1e-3) / 1e9, 3),
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs / peak, 4), "bytes_per_state": 8}}
+
+
+def measure_learned_quick(pd, torch, wl):
+    """The learned start on the 4x4 t-t' cluster, shortened for the default line: trained on the library's
+    own ground states at U = 2, 4, 6, 10 (half filling), used at the unseen U = 5; fixed-point Lanczos to
+    E0 at 1e-10 from the learned start (its build included) against the same from a random start."""
+    from paper_1707_03974_gb300 import learned
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    t0 = time.perf_counter()
+    sets = []
+    for U in (2.0, 4.0, 6.0, 10.0):
+        h = pd.Handle(cl.L, cl.bonds, cl.t, U, 8, 8)
+        _, psi = learned.ground_state(h, tol=1e-6)
+        sets.append(learned.sample(h, psi, 500000, seed=int(U)))
+        del psi
+        h.close()
+        torch.cuda.empty_cache()
+    t_data = time.perf_counter() - t0
+    m = pd.Mlp(32, seed=1)
+    rep = learned.train(m, sets, steps=600, batch=32768, lr=2e-3)
+    h = pd.Handle(cl.L, cl.bonds, cl.t, 5.0, 8, 8)
+    learned.tune(h)
+    rnd = learned.solve_from(h, torch.int64, seed=0)
+    v0, t_build = learned._timed_start(m, h, torch.int64)
+    got = learned.solve_from(h, torch.int64, v0=v0)
+    got["seconds"] += t_build
+    del v0
+    h.close()
+    m.close()
+    torch.cuda.empty_cache()
+    return {"workload": "learned start, 4x4 t-t' U = 5 (8,8), trained at U = 2, 4, 6, 10",
+            "data_seconds": round(t_data, 3), "train_seconds": round(rep.seconds, 3),
+            "iterations_learned_fx64": got["iterations"], "iterations_random_fx64": rnd["iterations"],
+            "seconds_learned_fx64_incl_start": round(got["seconds"], 4), "seconds_random_fx64": round(rnd["seconds"], 4),
+            "start_vector_seconds": round(t_build, 4), "abs_E0_diff": abs(got["E0"] - rnd["E0"]),
+            "converged": bool(got["converged"] and rnd["converged"])}
+
+
+def measure_batch64(pd, torch, wl, steps: int, warmup: int, vdt):
+    """64 independent 12-site problems solved together: instances/s to E0 at 1e-10 (the persistent
+    batched solver), the per-step time with every instance active, and the batched H·v against HBM."""
     insts = wl.draw_batch_instances(64)
     hs = [pd.Handle(i.cluster.L, i.cluster.bonds, i.cluster.t, i.U, i.N_up, i.N_dn) for i in insts]
     b = pd.Batch(hs)
-    vdt = {"f64": torch.float64, "fx64": torch.int64}.get(args.dtype, torch.int64)
     x = torch.zeros(b.total, dtype=torch.float64, device="cuda")
     x.uniform_(-0.5, 0.5)
     if vdt == torch.int64:
@@ -666,23 +795,23 @@ def run_batch(args, world, rank, local):
         x = xs
     y = torch.empty_like(x)
     tuned = pd.hubbard_batch_autotune(b, x, y, reps=3)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         pd.hubbard_batch_apply(b, x, y)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         pd.hubbard_batch_apply(b, x, y)
     e1.record()
     torch.cuda.synchronize()
-    hv_ms = e0.elapsed_time(e1) / args.steps
+    hv_ms = e0.elapsed_time(e1) / steps
     gold = None
     try:
         gold = [r["E0"] for r in json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_energies.json")))["batch64"]]
     except Exception:
         pass
     times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         E0, infos, status = pd.lanczos_batch_ground_state(b, maxit=2000, tol=1e-10, dtype=vdt, seed=0, check_every=10)
@@ -692,29 +821,46 @@ def run_batch(args, world, rank, local):
     D_total = sum(h.D for h in hs)
     # one persistent-kernel step with every instance active: the difference of two runs without a tolerance
     per = {}
-    for steps in (2, 34):
+    for n_steps in (2, 34):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pd.lanczos_batch_ground_state(b, maxit=steps, tol=0.0, dtype=vdt, seed=0, check_every=10)
+        pd.lanczos_batch_ground_state(b, maxit=n_steps, tol=0.0, dtype=vdt, seed=0, check_every=10)
         torch.cuda.synchronize()
-        per[steps] = time.perf_counter() - t0
+        per[n_steps] = time.perf_counter() - t0
     step_ms = (per[34] - per[2]) / 32 * 1e3
     err = max(abs(e - g) / max(1, abs(g)) for e, g in zip(E0, gold)) if gold else None
-    out = {"metric": "batched Lanczos instances/s to E0 at 1e-10", "value": round(64 / solve_s, 3), "unit": "instances/s",
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "int64" if vdt == torch.int64 else "f64", "data": "synthetic (seeded draws)",
-           "config": {"workload": "64 x 12-site Hubbard (ring-12 / 3x4), N_sigma in 3..6, U in [0,12)",
-                      "D_total": D_total, "vector_dtype": args.dtype},
-           "solve_seconds": round(solve_s, 4), "status": status,
-           "iterations_max": max(i["iterations"] for i in infos), "max_rel_err_vs_oracle": err,
-           "step_ms_all_active": round(step_ms, 4),
-           "step_gstates_per_s_all_active": round(D_total / (step_ms * 1e-3) / 1e9, 3),
-           "batched_hv_ms": round(hv_ms, 4), "batched_hv_gstates_per_s": round(D_total / (hv_ms * 1e-3) / 1e9, 3),
-           "batched_hv_config": tuned}
-    print(json.dumps(out))
+    peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    hv_gbs = 16 * D_total / (hv_ms * 1e-3) / 1e9
     b.close()
     for h in hs:
         h.close()
+    return {"instances_per_s": round(64 / solve_s, 3), "solve_seconds": round(solve_s, 4), "status": status,
+            "iterations_max": max(i["iterations"] for i in infos), "max_rel_err_vs_oracle": err, "D_total": D_total,
+            "step_ms_all_active": round(step_ms, 4),
+            "step_gstates_per_s_all_active": round(D_total / (step_ms * 1e-3) / 1e9, 3),
+            "batched_hv_ms": round(hv_ms, 4), "batched_hv_gstates_per_s": round(D_total / (hv_ms * 1e-3) / 1e9, 3),
+            "batched_hv_roofline": {"bound": "hbm", "achieved": round(hv_gbs, 1), "peak": peak, "unit": "GB/s",
+                                    "frac": round(hv_gbs / peak, 4), "bytes_per_state": 16},
+            "batched_hv_config": tuned}
+
+
+def run_batch(args, world, rank, local):
+    """64 independent 12-site problems solved together (the persistent batched solver)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1707_03974_gb300.build import build
+    build()
+    import paper_1707_03974_gb300 as pd
+    import workloads as wl
+    vdt = {"f64": torch.float64, "fx64": torch.int64}.get(args.dtype, torch.int64)
+    r = measure_batch64(pd, torch, wl, args.steps, args.warmup, vdt)
+    out = {"metric": "batched Lanczos instances/s to E0 at 1e-10", "value": r["instances_per_s"],
+           "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64" if vdt == torch.int64 else "f64",
+           "data": "synthetic (seeded draws)",
+           "config": {"workload": "64 x 12-site Hubbard (ring-12 / 3x4), N_sigma in 3..6, U in [0,12)",
+                      "D_total": r["D_total"], "vector_dtype": args.dtype}, **r}
+    print(json.dumps(out))
 
 
 def run_learned(args, world, rank, local):
@@ -857,6 +1003,40 @@ def run_green(args, world, rank, local):
     h.close()
 
 
+def run_tcgemm(args, local):
+    """The training product of the start-vector network on the tensor cores: C[4096 x 128] =
+    A[4096 x 4096] B[128 x 4096]^T (bf16 operands, float32 accumulation in tensor memory), the shape
+    of a layer-2 weight product over a 4096-state slab, through mlp_tc_gemm."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1707_03974_gb300.build import build
+    build()
+    import paper_1707_03974_gb300 as pd
+    g = torch.Generator().manual_seed(0)
+    M, N, K = 4096, 128, 4096
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    for _ in range(args.warmup):
+        C = pd.mlp_tc_gemm(A, B)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        C = pd.mlp_tc_gemm(A, B)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    err = (C.double() - A.double() @ B.double().T).abs().max().item()
+    peaks = measured_peaks() or {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+    print(json.dumps({"metric": "tcgen05 training product TFLOP/s", "value": round(tf, 3), "unit": "TFLOP/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+                      "config": {"workload": "tc_gemm_4096x128x4096_bf16"}, "max_abs_err": err,
+                      "roofline": {"bound": "tensor", "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
+                                   "frac": round(tf / peak, 4), "kernel": "k_tc_gemm<128>"}}))
+
+
 def run_ceilings(args, local):
     """The on-chip ceilings alone (one JSON line): the denominators of the H·v's on-chip rooflines."""
     import torch
@@ -878,6 +1058,10 @@ def main():
     if args.workload == "ceilings" and args.impl == "ours":
         if rank == 0:
             run_ceilings(args, local)
+        return
+    if args.workload == "tcgemm" and args.impl == "ours":
+        if rank == 0:
+            run_tcgemm(args, local)
         return
     if args.workload == "learned4x4" and args.impl == "ours":
         if rank == 0:

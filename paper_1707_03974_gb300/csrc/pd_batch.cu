@@ -450,6 +450,7 @@ struct PState {
     int withhold;            // CTA that leaves before its first arrival (the wait self-test), -1: none
     const uint64_t *up_prefix;  // split form: prefix sums of the spin-up items
     int up_W, up_S;             // split form: spin-up columns per block and row slots (up_W * up_S threads)
+    I128 *item_part;            // [items of the fused pass][8 warps]: per-warp partials of <w, v>
 };
 
 // Store hook of the H·v (fixed point): w = H v - beta_prev vprev and the exact
@@ -501,6 +502,21 @@ __device__ __forceinline__ void slice_x4(uint64_t e0, uint64_t e1, Fn f) {
         f(e + 3 * T);
     }
     for (; e < e1; e += T) f(e);
+}
+
+// The next item at or after `it` (items of this CTA are it, it + G, ...) whose
+// instance is active: items of an inactive instance are skipped in one jump.
+// Every thread of the CTA computes the same answer from the same data, so the
+// loop needs no barrier.  Returns false when no such item is left.
+__device__ __forceinline__ bool next_active_item(const uint64_t *pre, int n, const int *active, uint64_t total,
+                                                 unsigned G, uint64_t &it, int &k) {
+    while (it < total) {
+        k = find_inst(pre, n, it);
+        if (active[k]) return true;
+        const uint64_t end = pre[k + 1];  // first item of the next instance
+        it += (end - it + G - 1) / G * G;
+    }
+    return false;
 }
 
 // first instance whose vector ends after element e (instances ordered by offset)
@@ -558,18 +574,25 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
         if (na == 0) break;  // every CTA reads the same flags (set before the last barrier)
         const int iv = j % 3, ip = (j + 2) % 3, iw = (j + 1) % 3;
         // ---------------- phase A: H·v + first vector pass ----------------
-        for (int k = threadIdx.x; k < p.n; k += blockDim.x)
-            for (int q = 0; q < 3; ++q) p.part[((uint64_t)k * G + blockIdx.x) * 3 + q] = I128();
         typename std::conditional<FX, FxStepEpi, F64StepEpi>::type epi{};
         int cur = -1;
-        auto flush = [&](int k) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        // the warp's partial <w, v> of item `it`, then a fresh accumulator (no CTA barrier)
+        auto item_done = [&](uint64_t it) {
             if constexpr (FX) {
-                const I128 a = block_sum128(epi.swv);
-                if (threadIdx.x == 0) p.part[((uint64_t)k * G + blockIdx.x) * 3] = a;
+                I128 v = epi.swv;
+                for (int o = 16; o > 0; o >>= 1) {
+                    I128 t;
+                    t.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+                    t.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+                    i128_add(v, t);
+                }
+                if (lane == 0) p.item_part[it * (kPThreads / 32) + warp] = v;
                 epi.swv = I128();
             } else {
-                const double a = block_sum_d(epi.swv);
-                if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3)[0] = a;
+                double v = epi.swv;
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) reinterpret_cast<double *>(p.item_part + it * (kPThreads / 32) + warp)[0] = v;
                 epi.swv = 0.0;
             }
         };
@@ -593,14 +616,10 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
                 epi.bprev = bp;
             }
         };
+        int k = 0;
         if constexpr (SPLIT) {
             // row pass of every active instance: w = diag + spin-down hops
-            for (uint64_t it = blockIdx.x; it < n_items; it += G) {
-                __syncthreads();
-                if (threadIdx.x == 0) s_k = find_inst(prefix, p.n, it);
-                __syncthreads();
-                const int k = s_k;
-                if (!p.active[k]) continue;
+            for (uint64_t it = blockIdx.x; next_active_item(prefix, p.n, p.active, n_items, G, it, k); it += G) {
                 if (k != cur) enter(k, true);
                 hv_fx_wb_group<R, NC>(s_inst.fx, V + iv * p.stride + s_inst.off, V + iw * p.stride + s_inst.off,
                                       it - prefix[k], smem);
@@ -609,16 +628,8 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
             // spin-up pass; its hook adds - beta vprev and accumulates <w, v>
             cur = -1;
             const uint64_t n_up = up_prefix[p.n];
-            for (uint64_t it = blockIdx.x; it < n_up; it += G) {
-                __syncthreads();
-                if (threadIdx.x == 0) s_k = find_inst(up_prefix, p.n, it);
-                __syncthreads();
-                const int k = s_k;
-                if (!p.active[k]) continue;
-                if (k != cur) {
-                    if (cur >= 0) flush(cur);
-                    enter(k, false);
-                }
+            for (uint64_t it = blockIdx.x; next_active_item(up_prefix, p.n, p.active, n_up, G, it, k); it += G) {
+                if (k != cur) enter(k, false);
                 uint64_t jb, g;
                 up_item_of(s_inst.fx, it - up_prefix[k], p.up_S * 2, &jb, &g);
                 const int64_t *v = V + iv * p.stride + s_inst.off;
@@ -626,48 +637,45 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
                     hv_fx_up_item<2, NC, true, 2, FxStepEpi>(s_inst.fx, v, epi.w, jb, g, p.up_W, p.up_S, smem, &epi);
                 else
                     hv_fx_up_item<2, NC, true, 1, FxStepEpi>(s_inst.fx, v, epi.w, jb, g, p.up_W, p.up_S, smem, &epi);
+                item_done(it);
             }
         } else {
-            for (uint64_t it = blockIdx.x; it < n_items; it += G) {
-                __syncthreads();
-                if (threadIdx.x == 0) s_k = find_inst(prefix, p.n, it);
-                __syncthreads();
-                const int k = s_k;
-                if (!p.active[k]) continue;  // uniform across the CTA
-                if (k != cur) {
-                    if (cur >= 0) flush(cur);
-                    enter(k, FX);
-                }
+            for (uint64_t it = blockIdx.x; next_active_item(prefix, p.n, p.active, n_items, G, it, k); it += G) {
+                if (k != cur) enter(k, FX);
                 const uint64_t g = it - prefix[k];
                 const T *v = V + iv * p.stride + s_inst.off;
                 if constexpr (FX)
                     hv_fx_group<R, NC, true, true, FxStepEpi>(s_inst.fx, v, nullptr, g, smem, &epi);
                 else
                     hv_group<R, double, true, true, F64StepEpi>(s_inst.f64, v, nullptr, g, smem, &epi);
+                item_done(it);
             }
         }
-        if (cur >= 0) flush(cur);
         if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
+        // items whose warp partials hold <w, v>: the fused pass's, or the spin-up pass's in the split form
+        const uint64_t *epre = SPLIT ? up_prefix : prefix;
         // ---------------- phase B: alpha = <w, v>; w -= alpha v; partial ||w||^2 ----------------
         for (int k = threadIdx.x; k < p.n; k += blockDim.x) p.part[((uint64_t)k * G + blockIdx.x) * 3 + 1] = I128();
         if (c0 < c1) {
             for (int k = inst_at(p.inst, p.n, c0); k < p.n && p.inst[k].off < c1; ++k) {
                 if (!p.active[k]) continue;
                 const Inst &in = p.inst[k];
+                const uint64_t q0 = epre[k] * (kPThreads / 32), q1 = epre[k + 1] * (kPThreads / 32);
                 if constexpr (FX) {
                     I128 sa;
-                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) i128_add(sa, p.part[((uint64_t)k * G + b) * 3]);
+                    for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) i128_add(sa, p.item_part[q]);
                     sa = block_sum128(sa);
                     if (threadIdx.x == 0) s_ab[0] = pdx::dd_value(pdx::dd_of_i128(sa, -2 * in.F));
                 } else {
                     double sa = 0.0;
-                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x)
-                        sa += reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3)[0];
+                    for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x)
+                        sa += reinterpret_cast<const double *>(p.item_part + q)[0];
                     sa = block_sum_d(sa);
                     if (threadIdx.x == 0) s_ab[0] = sa;
                 }
                 __syncthreads();
                 const double al = s_ab[0];
+                if (in.off >= c0 && threadIdx.x == 0) p.alpha[(uint64_t)k * p.maxit1 + j] = al;  // the owner
                 const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
                 T *w = V + iw * p.stride;
                 const T *v = V + iv * p.stride;
@@ -702,39 +710,28 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
                 if (!p.active[k]) continue;
                 const Inst &in = p.inst[k];
                 if constexpr (FX) {
-                    I128 sa, sb;
-                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
-                        i128_add(sa, p.part[((uint64_t)k * G + b) * 3]);
-                        i128_add(sb, p.part[((uint64_t)k * G + b) * 3 + 1]);
-                    }
-                    sa = block_sum128(sa);
+                    I128 sb;
+                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) i128_add(sb, p.part[((uint64_t)k * G + b) * 3 + 1]);
                     sb = block_sum128(sb);
                     if (threadIdx.x == 0) {
-                        s_ab[0] = pdx::dd_value(pdx::dd_of_i128(sa, -2 * in.F));
+                        s_ab[0] = p.alpha[(uint64_t)k * p.maxit1 + j];
                         const double b2 = pdx::dd_value(pdx::dd_of_i128(sb, -2 * in.F));
                         s_ab[1] = b2 > 0.0 ? sqrt(b2) : 0.0;
                     }
                 } else {
-                    double sa = 0.0, sb = 0.0;
-                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
-                        const double *q = reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3);
-                        sa += q[0];
-                        sb += q[2];
-                    }
-                    sa = block_sum_d(sa);
+                    double sb = 0.0;
+                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x)
+                        sb += reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3)[2];
                     sb = block_sum_d(sb);
                     if (threadIdx.x == 0) {
-                        s_ab[0] = sa;
+                        s_ab[0] = p.alpha[(uint64_t)k * p.maxit1 + j];
                         s_ab[1] = sqrt(sb);
                     }
                 }
                 __syncthreads();
                 const double al = s_ab[0], be = s_ab[1];
                 const bool owner = in.off >= c0;  // this CTA holds the instance's first element
-                if (owner && threadIdx.x == 0) {
-                    p.alpha[(uint64_t)k * p.maxit1 + j] = al;
-                    p.beta[(uint64_t)k * p.maxit1 + j] = be;
-                }
+                if (owner && threadIdx.x == 0) p.beta[(uint64_t)k * p.maxit1 + j] = be;  // alpha: phase B
                 const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
                 T *w = V + iw * p.stride;
                 if constexpr (FX) {
@@ -1187,9 +1184,21 @@ namespace {
 
 // ---------------- batched Lanczos (host) ----------------
 struct BatchWs {
-    uint64_t vec, part_start, part, ab, tri, dbl, ints, sync, total;
+    uint64_t vec, part_start, part, item, ab, tri, dbl, ints, sync, total;
     int nb, gmax;
 };
+
+// items of the pass that carries the first reduction, at most: rows of every instance (one-kernel
+// form, one row per item) or the spin-up items of the persistent split shape (128 columns per block
+// at one column per thread, four rows per item)
+uint64_t max_epi_items(const hb_batch *b) {
+    uint64_t rows = 0, up = 0;
+    for (hb_handle h : b->h) {
+        rows += h->D_up;
+        up += (h->D_dn + 127) / 128 * ((h->D_up + 3) / 4);
+    }
+    return std::max(rows, up);
+}
 
 static BatchWs batch_layout_ws(hb_batch_handle b, const hb_lanczos_opts *o) {
     BatchWs L;
@@ -1200,7 +1209,8 @@ static BatchWs batch_layout_ws(hb_batch_handle b, const hb_lanczos_opts *o) {
     L.vec = 0;
     L.part_start = L.vec + 3 * align256(b->total * 8);
     L.part = L.part_start + align256(n * L.nb * 16);
-    L.ab = L.part + align256(n * L.gmax * 3 * 16);
+    L.item = L.part + align256(n * L.gmax * 3 * 16);
+    L.ab = L.item + align256(max_epi_items(b) * (kPThreads / 32) * 16);
     L.tri = L.ab + align256(n * m1 * 8 * 2);
     L.dbl = L.tri + align256(n * 6 * m1 * 8);
     L.ints = L.dbl + align256(n * 2 * 8);
@@ -1270,9 +1280,9 @@ hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, 
     const int R = split ? (b->rows == 1 ? 1 : 2) : (b->rows == 1 ? 1 : b->rows == 4 ? 4 : 2);
     // the spin-up shape of the persistent kernel: kPThreads threads, two rows per thread
     const int saved_W = b->up_W, saved_S = b->up_S, saved_RR = b->up_RR;
-    if (split) {
-        b->up_W = (b->up_W * b->up_S == kPThreads && b->up_RR == 2) ? b->up_W : 128;
-        b->up_S = kPThreads / b->up_W;
+    if (split) {  // the shape max_epi_items counts with
+        b->up_W = 128;
+        b->up_S = kPThreads / 128;
         b->up_RR = 2;
     }
     st = build_desc(b, R);  // items of R rows and the spin-up items of that shape (batch_prepare rebuilds for apply)
@@ -1324,6 +1334,7 @@ hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, 
     p.up_prefix = b->d_up_prefix;
     p.up_W = up_W;
     p.up_S = up_S;
+    p.item_part = reinterpret_cast<I128 *>(ws + L.item);
 
     cudaStream_t cs;
     PD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
