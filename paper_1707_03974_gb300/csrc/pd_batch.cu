@@ -486,22 +486,30 @@ struct F64StepEpi {
 
 constexpr int kPThreads = 256;
 constexpr int kSmemPrefix = 512;  // batches of up to this many instances keep their item prefix sums in shared memory
+constexpr int kTriSmem = 512;     // Lanczos lengths up to this are checked with the tridiagonal in shared memory
+constexpr size_t kTriSmemBytes = (size_t)8 * kTriSmem * 8;  // alpha, beta, six work arrays
 
-// f(e) for every element e of [e0, e1) handled by this thread: four elements
-// (e, e + T, e + 2T, e + 3T) per round so that each thread keeps several loads
-// in flight, then the remainder one by one.  f(e) must not depend on another
-// element's result.
-template <typename Fn>
-__device__ __forceinline__ void slice_x4(uint64_t e0, uint64_t e1, Fn f) {
-    const uint64_t T = blockDim.x;
+// w[e] = f(w[e], v[e]) for every element e of [e0, e1) handled by this thread
+// (v may be null: f then gets 0): the loads of four elements (e, e + T, e + 2T,
+// e + 3T) are issued before any of their stores, so each thread keeps eight
+// loads in flight (the pointers are restrict: w and v never overlap).  f may
+// accumulate on the side; it must not depend on another element's result.
+template <typename T, typename Fn>
+__device__ __forceinline__ void slice_update(uint64_t e0, uint64_t e1, T *__restrict__ w, const T *__restrict__ v,
+                                             Fn f) {
+    const uint64_t Tn = blockDim.x;
     uint64_t e = e0 + threadIdx.x;
-    for (; e + 3 * T < e1; e += 4 * T) {
-        f(e);
-        f(e + T);
-        f(e + 2 * T);
-        f(e + 3 * T);
+    for (; e + 3 * Tn < e1; e += 4 * Tn) {
+        T wv[4], vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            wv[u] = w[e + u * Tn];
+            vv[u] = v ? v[e + u * Tn] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[e + u * Tn] = f(wv[u], vv[u]);
     }
-    for (; e < e1; e += T) f(e);
+    for (; e < e1; e += Tn) w[e] = f(w[e], v ? v[e] : T(0));
 }
 
 // The next item at or after `it` (items of this CTA are it, it + G, ...) whose
@@ -682,19 +690,19 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
                 if constexpr (FX) {
                     const FxCoef ca = fx_coef_dev(al);
                     I128 acc;
-                    slice_x4(e0, e1, [&](uint64_t e) {
-                        const int64_t wi = w[e] - fx_mul(v[e], ca.K, ca.G);
-                        w[e] = wi;
+                    slice_update<int64_t>(e0, e1, w, v, [&](int64_t wv, int64_t vv) {
+                        const int64_t wi = wv - fx_mul(vv, ca.K, ca.G);
                         i128_add_prod(acc, wi, wi);
+                        return wi;
                     });
                     acc = block_sum128(acc);
                     if (threadIdx.x == 0) p.part[((uint64_t)k * G + blockIdx.x) * 3 + 1] = acc;
                 } else {
                     double acc = 0.0;
-                    slice_x4(e0, e1, [&](uint64_t e) {
-                        const double wi = w[e] - al * v[e];
-                        w[e] = wi;
+                    slice_update<double>(e0, e1, w, v, [&](double wv, double vv) {
+                        const double wi = wv - al * vv;
                         acc = fma(wi, wi, acc);
+                        return wi;
                     });
                     acc = block_sum_d(acc);
                     if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3 + 1)[0] = acc;
@@ -736,10 +744,10 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
                 T *w = V + iw * p.stride;
                 if constexpr (FX) {
                     const FxCoef cf = fx_coef_dev(be != 0.0 ? 1.0 / be : 0.0);
-                    slice_x4(e0, e1, [&](uint64_t e) { w[e] = fx_mul(w[e], cf.K, cf.G); });
+                    slice_update<int64_t>(e0, e1, w, nullptr, [&](int64_t wv, int64_t) { return fx_mul(wv, cf.K, cf.G); });
                 } else {
                     const double f = be != 0.0 ? 1.0 / be : 0.0;
-                    slice_x4(e0, e1, [&](uint64_t e) { w[e] *= f; });
+                    slice_update<double>(e0, e1, w, nullptr, [&](double wv, double) { return wv * f; });
                 }
                 const bool last = j + 1 >= p.maxit;
                 if (owner && (check || be == 0.0 || (uint64_t)(j + 1) >= in.D || last)) {
@@ -748,8 +756,20 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
                     if (threadIdx.x < 32) {
                         double th = 0.0, sl = 0.0;
                         const int nn = j + 1;
-                        tri_lowest_warp(p.alpha + (uint64_t)k * p.maxit1, p.beta + (uint64_t)k * p.maxit1, nn,
-                                        p.tri_ws + (uint64_t)k * 6 * p.maxit1, &th, &sl);
+                        const double *ga = p.alpha + (uint64_t)k * p.maxit1, *gb = p.beta + (uint64_t)k * p.maxit1;
+                        if (nn <= kTriSmem) {
+                            // the coefficients and the solver's work arrays in shared memory (free during this
+                            // phase): every dependent access of the sweeps stays on chip
+                            double *sa = reinterpret_cast<double *>(smem), *sb = sa + kTriSmem, *sw = sb + kTriSmem;
+                            for (int i = threadIdx.x; i < nn; i += 32) {
+                                sa[i] = ga[i];
+                                sb[i] = gb[i];
+                            }
+                            __syncwarp();
+                            tri_lowest_warp(sa, sb, nn, sw, &th, &sl);
+                        } else {
+                            tri_lowest_warp(ga, gb, nn, p.tri_ws + (uint64_t)k * 6 * p.maxit1, &th, &sl);
+                        }
                         if (threadIdx.x == 0) {
                             const double r = be * fabs(sl);
                             p.theta[k] = th;
@@ -1287,7 +1307,9 @@ hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, 
     }
     st = build_desc(b, R);  // items of R rows and the spin-up items of that shape (batch_prepare rebuilds for apply)
     const int up_W = b->up_W, up_S = b->up_S;
-    const size_t smem = split ? std::max(batch_row_smem(b, R), batch_up_smem(b)) : batch_smem(b, R, FX ? HB_FX64 : HB_F64);
+    // dynamic shared memory: the H·v phases' needs, or the tridiagonal check's, whichever is larger
+    const size_t smem = std::max(kTriSmemBytes, split ? std::max(batch_row_smem(b, R), batch_up_smem(b))
+                                                      : batch_smem(b, R, FX ? HB_FX64 : HB_F64));
     b->up_W = saved_W, b->up_S = saved_S, b->up_RR = saved_RR;
     if (st != HB_OK) return st;
     void *kern = nullptr;
