@@ -307,124 +307,168 @@ __device__ bool grid_barrier(GridSync *gs, unsigned long long limit_ns, unsigned
 }
 
 // ---- lowest eigenpair of the Lanczos tridiagonal, on the device (one warp) ----
-__device__ int sturm_below_dev(const double *a, const double *b, int n, double x) {
-    int c = 0;
-    double q = 1.0;
-    for (int i = 0; i < n; ++i) {
-        const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
-        q = (a[i] - x) - (i > 0 ? bb / q : 0.0);
-        if (q == 0.0) q = -DBL_EPSILON * (fabs(a[i]) + fabs(x) + DBL_MIN);
-        if (q < 0.0) ++c;
-    }
-    return c;
-}
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the check is
+// written to need few FP64 instructions per row: the Sturm counts and Newton
+// corrections come from the three-term recurrence of the leading principal
+// minors (no division per row), and the eigenvector's last component from one
+// twisted factorisation instead of inverse iteration.
 
-// (T - theta I) z = z in place, Gaussian elimination with partial pivoting on
-// the tridiagonal (row interchanges as in LAPACK's gttrf); ws: 5 n doubles.
-__device__ void shifted_solve_dev(const double *a, const double *b, int n, double theta, double *z, double *ws) {
-    double *dl = ws, *d = ws + n, *du = ws + 2 * n, *du2 = ws + 3 * n;
-    double scale = 0.0;
+// p_i = det(T_i - x I) (T_i the leading i x i block; p_0 = 1) and its derivative
+// in x, by p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}; both are rescaled by a
+// power of two whenever they leave [2^-256, 2^256].  count = sign changes of
+// p_0 .. p_n = eigenvalues of T_n below x (a zero p_i takes the sign opposite
+// to p_{i-1}).  b2: squared off-diagonals.
+struct TriEval {
+    int count;
+    double p, dp;
+};
+__device__ __forceinline__ int exp_of(double v) { return ((__double2hiint(v) >> 20) & 0x7ff) - 1023; }
+__device__ TriEval tri_eval(const double *a, const double *b2, int n, double x) {
+    double p2 = 0.0, p1 = 1.0, d2 = 0.0, d1 = 0.0;
+    int s1 = 0, c = 0;
     for (int i = 0; i < n; ++i) {
-        d[i] = a[i] - theta;
-        scale = fmax(scale, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0));
-    }
-    for (int i = 0; i + 1 < n; ++i) dl[i] = du[i] = b[i];
-    const double tiny = DBL_EPSILON * (scale > 0 ? scale : 1.0);
-    double *swapped = ws + 4 * n;  // 1.0 where rows i and i+1 were interchanged
-    for (int i = 0; i + 1 < n; ++i) {
-        if (fabs(d[i]) >= fabs(dl[i])) {
-            if (d[i] == 0.0) d[i] = tiny;
-            const double f = dl[i] / d[i];
-            dl[i] = f;
-            d[i + 1] -= f * du[i];
-            if (i + 2 < n) du2[i] = 0.0;
-            swapped[i] = 0.0;
-        } else {
-            const double f = d[i] / dl[i];
-            d[i] = dl[i];
-            dl[i] = f;
-            const double tmp = du[i];
-            du[i] = d[i + 1];
-            d[i + 1] = tmp - f * d[i + 1];
-            if (i + 2 < n) {
-                du2[i] = du[i + 1];
-                du[i + 1] = -f * du[i + 1];
-            }
-            swapped[i] = 1.0;
+        const double bb = i > 0 ? b2[i - 1] : 0.0;
+        const double d = a[i] - x;
+        const double p = fma(d, p1, -bb * p2);
+        const double dp = fma(d, d1, -fma(bb, d2, p1));
+        const int s = p != 0.0 ? (p < 0.0 ? 1 : 0) : 1 - s1;
+        c += s != s1;
+        p2 = p1;
+        p1 = p;
+        d2 = d1;
+        d1 = dp;
+        s1 = s;
+        const int e = min(max(exp_of(p1), exp_of(d1)), 1022);
+        if (e > 256 || e < -256) {
+            const double f = __hiloint2double((1023 - e) << 20, 0);  // 2^-e, exact
+            p2 *= f;
+            p1 *= f;
+            d2 *= f;
+            d1 *= f;
         }
     }
-    if (d[n - 1] == 0.0) d[n - 1] = tiny;
-    for (int i = 0; i + 1 < n; ++i) {
-        if (swapped[i] == 0.0) {
-            z[i + 1] -= dl[i] * z[i];
-        } else {
-            const double tmp = z[i];
-            z[i] = z[i + 1];
-            z[i + 1] = tmp - dl[i] * z[i];
-        }
-    }
-    z[n - 1] /= d[n - 1];
-    if (n > 1) z[n - 2] = (z[n - 2] - du[n - 2] * z[n - 1]) / d[n - 2];
-    for (int i = n - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / d[i];
+    return {c, p1, d1};
 }
 
-// theta = lowest eigenvalue of T_n (alpha a[0..n), beta b[0..n-1)) by multisection:
-// the 32 lanes count the eigenvalues below 32 points of the bracket with the
-// Sturm sequence, and the bracket shrinks to the two points around the first
-// count >= 1, until it stops shrinking.  s_last: last component of the
-// normalised eigenvector by three steps of inverse iteration from all ones
-// (lane 0; ws: 6 n doubles).  Called by all 32 lanes of one warp.
-__device__ void tri_lowest_warp(const double *a, const double *b, int n, double *ws, double *theta,
-                                double *s_last) {
+__device__ __forceinline__ double warp_min_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// theta = lowest eigenvalue of T_n (diagonal a[0..n), squared off-diagonal
+// b2[0..n-1), off-diagonal b[0..n-1)) and s_last = |last component| of its
+// normalised eigenvector.  Called by all 32 lanes of one warp; dp, dm: n
+// doubles each (work).
+//
+// theta: each pass evaluates the recurrence at 32 points of the bracket
+// [lo, hi] (lane 0 at lo).  A point with no eigenvalue below it is a lower
+// bound, and so is its Newton iterate on det(T_n - x I): left of the smallest
+// root of a polynomial with real roots, Newton steps rise monotonically
+// towards that root.  A point with an eigenvalue below it is an upper bound.
+// Passes stop when lo's Newton correction is at rounding level, or the bracket
+// stops shrinking.
+//
+// s_last: the twisted factorisation of T_n - theta I (Dhillon and Parlett):
+// forward pivots dp (lane 0) and backward pivots dm (lane 1) in one pass,
+// gamma_k = dp_k + dm_k - (a_k - theta), and the eigenvector solved from the
+// row k of smallest |gamma_k| outwards with z_k = 1.
+__device__ void tri_lowest_warp(const double *a, const double *b2, const double *b, int n, double *dp,
+                                double *dm, double *theta, double *s_last) {
     const int lane = threadIdx.x & 31;
     if (n == 1) {
         *theta = a[0];
         *s_last = 1.0;
         return;
     }
-    double lo = INFINITY, hi = -INFINITY;
+    double lo = INFINITY, hi = -INFINITY, amax = 0.0;
     for (int i = lane; i < n; i += 32) {
         const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0);
         lo = fmin(lo, a[i] - r);
         hi = fmax(hi, a[i] + r);
+        amax = fmax(amax, fabs(a[i]) + r);
+    }
+    lo = warp_min_d(lo);
+    hi = warp_max_d(hi);
+    amax = warp_max_d(amax);
+    for (int pass = 0; pass < 64; ++pass) {
+        const double x = lane == 0 ? lo : lo + (hi - lo) * ((double)lane / 32.0);
+        const TriEval ev = tri_eval(a, b2, n, x);
+        double up = INFINITY, down = -INFINITY;
+        bool small = false;
+        if (ev.count >= 1) {
+            up = x;
+        } else {
+            down = x;
+            if (ev.dp != 0.0) {
+                const double step = -ev.p / ev.dp;  // >= 0 below the smallest root
+                if (step > 0.0 && isfinite(step)) down = x + step;
+                small = !(fabs(step) > 4.0 * DBL_EPSILON * fmax(fabs(x), DBL_EPSILON * amax));
+            }
+        }
+        const bool stop = __shfl_sync(0xffffffffu, small ? 1 : 0, 0) != 0;  // lo's correction is negligible
+        const double nhi = fmin(hi, warp_min_d(up));
+        double nlo = fmax(lo, warp_max_d(down));
+        if (nlo > nhi) nlo = nhi;  // a Newton iterate past an upper bound is rounding
+        const bool progress = nhi - nlo < hi - lo;
+        if (progress) {
+            lo = nlo;
+            hi = nhi;
+        }
+        if (stop || !progress || !(hi - lo > 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)))) break;
+    }
+    const double th = lo;
+    // forward (lane 0) and backward (lane 1) pivots of T_n - th I
+    const double tiny = DBL_EPSILON * (amax > 0.0 ? amax : 1.0);
+    if (lane < 2) {
+        double prev = 1.0;
+        double *out = lane == 0 ? dp : dm;
+        for (int t = 0; t < n; ++t) {
+            const int i = lane == 0 ? t : n - 1 - t;
+            double d = a[i] - th;
+            if (t > 0) d -= b2[lane == 0 ? i - 1 : i] / prev;
+            if (d == 0.0) d = tiny;
+            out[i] = d;
+            prev = d;
+        }
+    }
+    __syncwarp();
+    double g = INFINITY;
+    int k = n;
+    for (int i = lane; i < n; i += 32) {
+        const double gi = fabs(dp[i] + dm[i] - (a[i] - th));
+        if (gi < g) {
+            g = gi;
+            k = i;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    for (int round = 0; round < 64; ++round) {
-        const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
-        const unsigned m = __ballot_sync(0xffffffffu, sturm_below_dev(a, b, n, x) >= 1);
-        double nlo, nhi;
-        if (m == 0) {
-            nlo = __shfl_sync(0xffffffffu, x, 31);
-            nhi = hi;
-        } else {
-            const int f = __ffs(m) - 1;
-            nhi = __shfl_sync(0xffffffffu, x, f);
-            const double xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
-            nlo = f > 0 ? xp : lo;
+        const double go = __shfl_xor_sync(0xffffffffu, g, o);
+        const int ko = __shfl_xor_sync(0xffffffffu, k, o);
+        if (go < g || (go == g && ko < k)) {
+            g = go;
+            k = ko;
         }
-        if (!(nhi - nlo < hi - lo)) break;  // no progress: the bracket is a few doubles wide
-        lo = fmax(lo, nlo);
-        hi = fmin(hi, nhi);
-        if (!(lo < hi)) break;
     }
-    const double th = 0.5 * (lo + hi);
-    if (lane == 0) {
-        double *z = ws + 5 * n;
-        for (int i = 0; i < n; ++i) z[i] = 1.0;
-        for (int it = 0; it < 3; ++it) {
-            shifted_solve_dev(a, b, n, th, z, ws);
-            double nrm = 0.0;
-            for (int i = 0; i < n; ++i) nrm += z[i] * z[i];
-            nrm = sqrt(nrm);
-            if (!(nrm > 0.0) || !isfinite(nrm)) break;
-            for (int i = 0; i < n; ++i) z[i] /= nrm;
+    if (k >= n) k = 0;  // every gamma was NaN: fall back to the first row
+    // z: lane 0 from row k towards row 0, lane 1 from row k towards row n - 1
+    double z = 1.0, ss = 0.0;
+    if (lane < 2) {
+        const int len = lane == 0 ? k : n - 1 - k;
+        for (int t = 0; t < len; ++t) {
+            const int i = lane == 0 ? k - 1 - t : k + t;
+            const double piv = lane == 0 ? dp[i] : dm[i + 1];
+            z = -(b[i] / piv) * z;
+            ss = fma(z, z, ss);
         }
-        *theta = th;
-        *s_last = z[n - 1];
     }
+    const double ss0 = __shfl_sync(0xffffffffu, ss, 0), ss1 = __shfl_sync(0xffffffffu, ss, 1);
+    const double zl = __shfl_sync(0xffffffffu, z, 1);
+    *theta = th;
+    *s_last = fabs(zl) / sqrt(1.0 + ss0 + ss1);
 }
 
 // ---- the persistent kernel ----
@@ -444,7 +488,7 @@ struct PState {
     double *alpha, *beta;    // [n][maxit1]
     double *theta, *res;     // [n]
     int *iters, *conv;       // [n]
-    double *tri_ws;          // [n][6 maxit1]
+    double *tri_ws;          // [n][3 maxit1]: beta^2 and the pivots of checks longer than kTriSmem
     GridSync *gs;
     unsigned long long limit_ns;
     int withhold;            // CTA that leaves before its first arrival (the wait self-test), -1: none
@@ -486,8 +530,8 @@ struct F64StepEpi {
 
 constexpr int kPThreads = 256;
 constexpr int kSmemPrefix = 512;  // batches of up to this many instances keep their item prefix sums in shared memory
-constexpr int kTriSmem = 512;     // Lanczos lengths up to this are checked with the tridiagonal in shared memory
-constexpr size_t kTriSmemBytes = (size_t)8 * kTriSmem * 8;  // alpha, beta, six work arrays
+constexpr int kTriSmem = 768;     // Lanczos lengths up to this are checked with the tridiagonal in shared memory
+constexpr size_t kTriSmemBytes = (size_t)5 * kTriSmem * 8;  // alpha, beta, beta^2 and two pivot arrays
 
 // w[e] = f(w[e], v[e]) for every element e of [e0, e1) handled by this thread
 // (v may be null: f then gets 0): the loads of four elements (e, e + T, e + 2T,
@@ -552,10 +596,12 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];  // filled by copy_inst, no constructor
     Inst &s_inst = *reinterpret_cast<Inst *>(s_inst_raw);
-    __shared__ int s_k;
     __shared__ double s_ab[2];
     __shared__ uint64_t s_prefix[kSmemPrefix + 1];  // item prefix sums, when the batch is small enough
     __shared__ uint64_t s_up_prefix[SPLIT ? kSmemPrefix + 1 : 1];
+    __shared__ uint64_t s_apre[2 * kPThreads];  // active elements' prefix sums (phases B and C)
+    __shared__ uint64_t s_wsum[kPThreads / 32];
+    const bool compact = p.n < 2 * kPThreads;
     const bool pre_smem = p.n <= kSmemPrefix;
     if (pre_smem)
         for (int k = threadIdx.x; k <= p.n; k += blockDim.x) {
@@ -662,131 +708,177 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
         if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
         // items whose warp partials hold <w, v>: the fused pass's, or the spin-up pass's in the split form
         const uint64_t *epre = SPLIT ? up_prefix : prefix;
+        // ---------------- slices of phases B and C ----------------
+        // Batches of fewer than 2 kPThreads instances split the elements of the instances active
+        // at this step evenly over the CTAs (s_apre: their exclusive prefix sums, taken from the
+        // flags as they stand after the last step's checks and kept for phase C, whose owners
+        // change the flags); larger batches split the whole batch vector.
+        if (compact) {
+            const int t = threadIdx.x, k0 = 2 * t, k1 = 2 * t + 1;
+            const uint64_t v0 = (k0 < p.n && p.active[k0]) ? p.inst[k0].D : 0;
+            const uint64_t v1 = (k1 < p.n && p.active[k1]) ? p.inst[k1].D : 0;
+            const uint64_t s = v0 + v1;
+            uint64_t incl = s;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((t & 31) >= o) incl += y;
+            }
+            if ((t & 31) == 31) s_wsum[t >> 5] = incl;
+            __syncthreads();
+            uint64_t base = 0;
+            for (int w = 0; w < (t >> 5); ++w) base += s_wsum[w];
+            const uint64_t excl = base + incl - s;
+            if (k0 <= p.n) s_apre[k0] = excl;
+            if (k1 <= p.n) s_apre[k1] = excl + v0;
+            __syncthreads();
+        }
+        // fn(k, e0, e1, owner) for each instance k this CTA updates: elements [e0, e1) of the
+        // batch vector; owner: the CTA holds the instance's first element of the split
+        auto for_slices = [&](auto &&fn) {
+            if (compact) {
+                const uint64_t A = s_apre[p.n];
+                const uint64_t pa = ((A + G - 1) / G + 3) & ~3ull;
+                const uint64_t a0 = min(A, (uint64_t)blockIdx.x * pa), a1 = min(A, a0 + pa);
+                if (a0 >= a1) return;
+                int lo = 0, hi = p.n - 1;  // first k with s_apre[k + 1] > a0
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_apre[mid + 1] > a0) hi = mid; else lo = mid + 1;
+                }
+                for (int k = lo; k < p.n && s_apre[k] < a1; ++k) {
+                    if (s_apre[k + 1] == s_apre[k]) continue;  // inactive at this step
+                    const uint64_t off = p.inst[k].off;
+                    fn(k, off + (max(a0, s_apre[k]) - s_apre[k]), off + (min(a1, s_apre[k + 1]) - s_apre[k]),
+                       s_apre[k] >= a0);
+                }
+            } else if (c0 < c1) {
+                for (int k = inst_at(p.inst, p.n, c0); k < p.n && p.inst[k].off < c1; ++k) {
+                    if (!p.active[k]) continue;
+                    const Inst &in = p.inst[k];
+                    fn(k, max(c0, in.off), min(c1, in.off + in.D), in.off >= c0);
+                }
+            }
+        };
         // ---------------- phase B: alpha = <w, v>; w -= alpha v; partial ||w||^2 ----------------
         for (int k = threadIdx.x; k < p.n; k += blockDim.x) p.part[((uint64_t)k * G + blockIdx.x) * 3 + 1] = I128();
-        if (c0 < c1) {
-            for (int k = inst_at(p.inst, p.n, c0); k < p.n && p.inst[k].off < c1; ++k) {
-                if (!p.active[k]) continue;
-                const Inst &in = p.inst[k];
-                const uint64_t q0 = epre[k] * (kPThreads / 32), q1 = epre[k + 1] * (kPThreads / 32);
-                if constexpr (FX) {
-                    I128 sa;
-                    for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) i128_add(sa, p.item_part[q]);
-                    sa = block_sum128(sa);
-                    if (threadIdx.x == 0) s_ab[0] = pdx::dd_value(pdx::dd_of_i128(sa, -2 * in.F));
-                } else {
-                    double sa = 0.0;
-                    for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x)
-                        sa += reinterpret_cast<const double *>(p.item_part + q)[0];
-                    sa = block_sum_d(sa);
-                    if (threadIdx.x == 0) s_ab[0] = sa;
-                }
-                __syncthreads();
-                const double al = s_ab[0];
-                if (in.off >= c0 && threadIdx.x == 0) p.alpha[(uint64_t)k * p.maxit1 + j] = al;  // the owner
-                const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
-                T *w = V + iw * p.stride;
-                const T *v = V + iv * p.stride;
-                if constexpr (FX) {
-                    const FxCoef ca = fx_coef_dev(al);
-                    I128 acc;
-                    slice_update<int64_t>(e0, e1, w, v, [&](int64_t wv, int64_t vv) {
-                        const int64_t wi = wv - fx_mul(vv, ca.K, ca.G);
-                        i128_add_prod(acc, wi, wi);
-                        return wi;
-                    });
-                    acc = block_sum128(acc);
-                    if (threadIdx.x == 0) p.part[((uint64_t)k * G + blockIdx.x) * 3 + 1] = acc;
-                } else {
-                    double acc = 0.0;
-                    slice_update<double>(e0, e1, w, v, [&](double wv, double vv) {
-                        const double wi = wv - al * vv;
-                        acc = fma(wi, wi, acc);
-                        return wi;
-                    });
-                    acc = block_sum_d(acc);
-                    if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3 + 1)[0] = acc;
-                }
-                __syncthreads();
+        for_slices([&](int k, uint64_t e0, uint64_t e1, bool owner) {
+            const int F = p.inst[k].F;
+            const uint64_t q0 = epre[k] * (kPThreads / 32), q1 = epre[k + 1] * (kPThreads / 32);
+            if constexpr (FX) {
+                I128 sa;
+                for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) i128_add(sa, p.item_part[q]);
+                sa = block_sum128(sa);
+                if (threadIdx.x == 0) s_ab[0] = pdx::dd_value(pdx::dd_of_i128(sa, -2 * F));
+            } else {
+                double sa = 0.0;
+                for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x)
+                    sa += reinterpret_cast<const double *>(p.item_part + q)[0];
+                sa = block_sum_d(sa);
+                if (threadIdx.x == 0) s_ab[0] = sa;
             }
-        }
+            __syncthreads();
+            const double al = s_ab[0];
+            if (owner && threadIdx.x == 0) p.alpha[(uint64_t)k * p.maxit1 + j] = al;
+            T *w = V + iw * p.stride;
+            const T *v = V + iv * p.stride;
+            if constexpr (FX) {
+                const FxCoef ca = fx_coef_dev(al);
+                I128 acc;
+                slice_update<int64_t>(e0, e1, w, v, [&](int64_t wv, int64_t vv) {
+                    const int64_t wi = wv - fx_mul(vv, ca.K, ca.G);
+                    i128_add_prod(acc, wi, wi);
+                    return wi;
+                });
+                acc = block_sum128(acc);
+                if (threadIdx.x == 0) p.part[((uint64_t)k * G + blockIdx.x) * 3 + 1] = acc;
+            } else {
+                double acc = 0.0;
+                slice_update<double>(e0, e1, w, v, [&](double wv, double vv) {
+                    const double wi = wv - al * vv;
+                    acc = fma(wi, wi, acc);
+                    return wi;
+                });
+                acc = block_sum_d(acc);
+                if (threadIdx.x == 0) reinterpret_cast<double *>(p.part + ((uint64_t)k * G + blockIdx.x) * 3 + 1)[0] = acc;
+            }
+            __syncthreads();
+        });
         if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
         // ---------------- phase C: alpha, beta; w = (w - alpha v) / beta; checks ----------------
         const bool check = (j + 1) % p.check_every == 0;
-        if (c0 < c1) {
-            for (int k = inst_at(p.inst, p.n, c0); k < p.n && p.inst[k].off < c1; ++k) {
-                if (!p.active[k]) continue;
-                const Inst &in = p.inst[k];
-                if constexpr (FX) {
-                    I128 sb;
-                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) i128_add(sb, p.part[((uint64_t)k * G + b) * 3 + 1]);
-                    sb = block_sum128(sb);
-                    if (threadIdx.x == 0) {
-                        s_ab[0] = p.alpha[(uint64_t)k * p.maxit1 + j];
-                        const double b2 = pdx::dd_value(pdx::dd_of_i128(sb, -2 * in.F));
-                        s_ab[1] = b2 > 0.0 ? sqrt(b2) : 0.0;
-                    }
-                } else {
-                    double sb = 0.0;
-                    for (unsigned b = threadIdx.x; b < G; b += blockDim.x)
-                        sb += reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3)[2];
-                    sb = block_sum_d(sb);
-                    if (threadIdx.x == 0) {
-                        s_ab[0] = p.alpha[(uint64_t)k * p.maxit1 + j];
-                        s_ab[1] = sqrt(sb);
-                    }
+        for_slices([&](int k, uint64_t e0, uint64_t e1, bool owner) {
+            const Inst &in = p.inst[k];
+            if constexpr (FX) {
+                I128 sb;
+                for (unsigned b = threadIdx.x; b < G; b += blockDim.x) i128_add(sb, p.part[((uint64_t)k * G + b) * 3 + 1]);
+                sb = block_sum128(sb);
+                if (threadIdx.x == 0) {
+                    const double b2 = pdx::dd_value(pdx::dd_of_i128(sb, -2 * in.F));
+                    s_ab[1] = b2 > 0.0 ? sqrt(b2) : 0.0;
                 }
-                __syncthreads();
-                const double al = s_ab[0], be = s_ab[1];
-                const bool owner = in.off >= c0;  // this CTA holds the instance's first element
-                if (owner && threadIdx.x == 0) p.beta[(uint64_t)k * p.maxit1 + j] = be;  // alpha: phase B
-                const uint64_t e0 = max(c0, in.off), e1 = min(c1, in.off + in.D);
-                T *w = V + iw * p.stride;
-                if constexpr (FX) {
-                    const FxCoef cf = fx_coef_dev(be != 0.0 ? 1.0 / be : 0.0);
-                    slice_update<int64_t>(e0, e1, w, nullptr, [&](int64_t wv, int64_t) { return fx_mul(wv, cf.K, cf.G); });
-                } else {
-                    const double f = be != 0.0 ? 1.0 / be : 0.0;
-                    slice_update<double>(e0, e1, w, nullptr, [&](double wv, double) { return wv * f; });
+            } else {
+                double sb = 0.0;
+                for (unsigned b = threadIdx.x; b < G; b += blockDim.x)
+                    sb += reinterpret_cast<const double *>(p.part + ((uint64_t)k * G + b) * 3)[2];
+                sb = block_sum_d(sb);
+                if (threadIdx.x == 0) {
+                    s_ab[1] = sqrt(sb);
                 }
-                const bool last = j + 1 >= p.maxit;
-                if (owner && (check || be == 0.0 || (uint64_t)(j + 1) >= in.D || last)) {
-                    __threadfence_block();
-                    __syncthreads();
-                    if (threadIdx.x < 32) {
-                        double th = 0.0, sl = 0.0;
-                        const int nn = j + 1;
-                        const double *ga = p.alpha + (uint64_t)k * p.maxit1, *gb = p.beta + (uint64_t)k * p.maxit1;
-                        if (nn <= kTriSmem) {
-                            // the coefficients and the solver's work arrays in shared memory (free during this
-                            // phase): every dependent access of the sweeps stays on chip
-                            double *sa = reinterpret_cast<double *>(smem), *sb = sa + kTriSmem, *sw = sb + kTriSmem;
-                            for (int i = threadIdx.x; i < nn; i += 32) {
-                                sa[i] = ga[i];
-                                sb[i] = gb[i];
-                            }
-                            __syncwarp();
-                            tri_lowest_warp(sa, sb, nn, sw, &th, &sl);
-                        } else {
-                            tri_lowest_warp(ga, gb, nn, p.tri_ws + (uint64_t)k * 6 * p.maxit1, &th, &sl);
-                        }
-                        if (threadIdx.x == 0) {
-                            const double r = be * fabs(sl);
-                            p.theta[k] = th;
-                            p.res[k] = r;
-                            p.iters[k] = nn;
-                            const bool done = (p.tol > 0 && r <= p.tol * fmax(1.0, fabs(th))) || be == 0.0 ||
-                                              (uint64_t)nn >= in.D;
-                            if (done) {
-                                p.conv[k] = 1;
-                                p.active[k] = 0;
-                            }
-                        }
-                    }
-                }
-                __syncthreads();
             }
-        }
+            __syncthreads();
+            const double be = s_ab[1];
+            if (owner && threadIdx.x == 0) p.beta[(uint64_t)k * p.maxit1 + j] = be;  // alpha: phase B
+            T *w = V + iw * p.stride;
+            if constexpr (FX) {
+                const FxCoef cf = fx_coef_dev(be != 0.0 ? 1.0 / be : 0.0);
+                slice_update<int64_t>(e0, e1, w, nullptr, [&](int64_t wv, int64_t) { return fx_mul(wv, cf.K, cf.G); });
+            } else {
+                const double f = be != 0.0 ? 1.0 / be : 0.0;
+                slice_update<double>(e0, e1, w, nullptr, [&](double wv, double) { return wv * f; });
+            }
+            const bool last = j + 1 >= p.maxit;
+            if (owner && (check || be == 0.0 || (uint64_t)(j + 1) >= in.D || last)) {
+                __threadfence_block();
+                __syncthreads();
+                if (threadIdx.x < 32) {
+                    double th = 0.0, sl = 0.0;
+                    const int nn = j + 1;
+                    const double *ga = p.alpha + (uint64_t)k * p.maxit1, *gb = p.beta + (uint64_t)k * p.maxit1;
+                    // the coefficients and the work arrays: shared memory (free during this phase) up to
+                    // kTriSmem steps, so every dependent access of the passes stays on chip; else global
+                    const bool on_chip = nn <= kTriSmem;
+                    double *sa = reinterpret_cast<double *>(smem);
+                    double *sb = on_chip ? sa + kTriSmem : nullptr;
+                    double *w0 = on_chip ? sa + 2 * kTriSmem : p.tri_ws + (uint64_t)k * 3 * p.maxit1;
+                    double *sb2 = w0, *sdp = w0 + (on_chip ? kTriSmem : p.maxit1), *sdm = sdp + (on_chip ? kTriSmem : p.maxit1);
+                    for (int i = threadIdx.x; i < nn; i += 32) {
+                        if (on_chip) {
+                            sa[i] = ga[i];
+                            sb[i] = gb[i];
+                        }
+                        sb2[i] = gb[i] * gb[i];
+                    }
+                    __syncwarp();
+                    if (on_chip)
+                        tri_lowest_warp(sa, sb2, sb, nn, sdp, sdm, &th, &sl);
+                    else
+                        tri_lowest_warp(ga, sb2, gb, nn, sdp, sdm, &th, &sl);
+                    if (threadIdx.x == 0) {
+                        const double r = be * fabs(sl);
+                        p.theta[k] = th;
+                        p.res[k] = r;
+                        p.iters[k] = nn;
+                        const bool done = (p.tol > 0 && r <= p.tol * fmax(1.0, fabs(th))) || be == 0.0 ||
+                                          (uint64_t)nn >= in.D;
+                        if (done) {
+                            p.conv[k] = 1;
+                            p.active[k] = 0;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        });
         if (!grid_barrier(p.gs, p.limit_ns, tag++)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1232,7 +1324,7 @@ static BatchWs batch_layout_ws(hb_batch_handle b, const hb_lanczos_opts *o) {
     L.item = L.part + align256(n * L.gmax * 3 * 16);
     L.ab = L.item + align256(max_epi_items(b) * (kPThreads / 32) * 16);
     L.tri = L.ab + align256(n * m1 * 8 * 2);
-    L.dbl = L.tri + align256(n * 6 * m1 * 8);
+    L.dbl = L.tri + align256(n * 3 * m1 * 8);
     L.ints = L.dbl + align256(n * 2 * 8);
     L.sync = L.ints + align256((3 * n + 2) * 4);
     L.total = L.sync + 256;
