@@ -529,6 +529,8 @@ struct F64StepEpi {
 };
 
 constexpr int kPThreads = 256;
+constexpr int kPUpRR = 4;        // spin-up rows per thread in the persistent kernel
+constexpr int kPMinBlocks = 4;    // CTAs per SM the persistent kernel's light variants are compiled for
 constexpr int kSmemPrefix = 512;  // batches of up to this many instances keep their item prefix sums in shared memory
 constexpr int kTriSmem = 768;     // Lanczos lengths up to this are checked with the tridiagonal in shared memory
 constexpr size_t kTriSmemBytes = (size_t)5 * kTriSmem * 8;  // alpha, beta, beta^2 and two pivot arrays
@@ -591,7 +593,7 @@ __device__ __forceinline__ int inst_at(const Inst *inst, int n, uint64_t e) {
 // holds its first element; barrier.  With fixed-point vectors both reductions
 // are exact 128-bit sums (converted to float64 once, through double-double).
 template <int R, int NC, bool FX, bool SPLIT>
-__global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) k_batch_lanczos(PState p) {
+__global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? kPMinBlocks : 3) k_batch_lanczos(PState p) {
     static_assert(FX || !SPLIT, "the split form is fixed point only");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) unsigned char s_inst_raw[sizeof(Inst)];  // filled by copy_inst, no constructor
@@ -685,12 +687,12 @@ __global__ void __launch_bounds__(kPThreads, (FX && NC <= 2 && R <= 2) ? 4 : 3) 
             for (uint64_t it = blockIdx.x; next_active_item(up_prefix, p.n, p.active, n_up, G, it, k); it += G) {
                 if (k != cur) enter(k, false);
                 uint64_t jb, g;
-                up_item_of(s_inst.fx, it - up_prefix[k], p.up_S * 2, &jb, &g);
+                up_item_of(s_inst.fx, it - up_prefix[k], p.up_S * kPUpRR, &jb, &g);
                 const int64_t *v = V + iv * p.stride + s_inst.off;
                 if (s_inst.fx.Dd % 2 == 0)
-                    hv_fx_up_item<2, NC, true, 2, FxStepEpi>(s_inst.fx, v, epi.w, jb, g, p.up_W, p.up_S, smem, &epi);
+                    hv_fx_up_item<kPUpRR, NC, true, 2, FxStepEpi>(s_inst.fx, v, epi.w, jb, g, p.up_W, p.up_S, smem, &epi);
                 else
-                    hv_fx_up_item<2, NC, true, 1, FxStepEpi>(s_inst.fx, v, epi.w, jb, g, p.up_W, p.up_S, smem, &epi);
+                    hv_fx_up_item<kPUpRR, NC, true, 1, FxStepEpi>(s_inst.fx, v, epi.w, jb, g, p.up_W, p.up_S, smem, &epi);
                 item_done(it);
             }
         } else {
@@ -1302,12 +1304,13 @@ struct BatchWs {
 
 // items of the pass that carries the first reduction, at most: rows of every instance (one-kernel
 // form, one row per item) or the spin-up items of the persistent split shape (128 columns per block
-// at one column per thread, four rows per item)
+// at one column per thread, kPThreads / 128 row slots of kPUpRR rows per item)
 uint64_t max_epi_items(const hb_batch *b) {
+    constexpr uint64_t rows_per_item = (kPThreads / 128) * kPUpRR;
     uint64_t rows = 0, up = 0;
     for (hb_handle h : b->h) {
         rows += h->D_up;
-        up += (h->D_dn + 127) / 128 * ((h->D_up + 3) / 4);
+        up += (h->D_dn + 127) / 128 * ((h->D_up + rows_per_item - 1) / rows_per_item);
     }
     return std::max(rows, up);
 }
@@ -1395,7 +1398,7 @@ hb_status batch_lanczos(hb_batch *b, const hb_lanczos_opts *o, void *workspace, 
     if (split) {  // the shape max_epi_items counts with
         b->up_W = 128;
         b->up_S = kPThreads / 128;
-        b->up_RR = 2;
+        b->up_RR = kPUpRR;
     }
     st = build_desc(b, R);  // items of R rows and the spin-up items of that shape (batch_prepare rebuilds for apply)
     const int up_W = b->up_W, up_S = b->up_S;
