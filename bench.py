@@ -290,7 +290,7 @@ def run_ours(args, world, rank, local):
     # region).  The copies run on a second stream into a ring of three device buffers, so the
     # copy for step j + 1 overlaps the compute of step j; step j waits for its own copy, and
     # a buffer is refilled only after the last step that read it (as v, then as vprev)
-    host_v = torch.empty(D, dtype=vdt, pin_memory=True)
+    host_v = pd.host_empty(D, vdt)  # page-locked, on huge pages (hb_host_alloc)
     host_v.copy_(V[nsteps % 3])
     host_ab = torch.empty(2, dtype=torch.float64, pin_memory=True)
     e2e_steps = max(3, min(args.steps, 10))
@@ -420,7 +420,8 @@ def run_ours(args, world, rank, local):
                 "h2d_bytes_per_step": D * host_bytes, "d2h_bytes_per_step": 16,
                 "step": "the general three-term step (v from the host, vprev and beta_prev resident), as timed above",
                 "output": "alpha and beta are read back each step; w stays on the device",
-                "overlap": "each step's input copy runs on a second stream while the previous step computes"},
+                "overlap": "each step's input copy runs on a second stream while the previous step computes",
+                "host_buffer": "hb_host_alloc: page-locked, 2 MiB-aligned, advised for huge pages"},
         "gpu_launches": int(launches.value),
         "clocks": clk,
         "recurrence_sane": sane,

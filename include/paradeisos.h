@@ -495,6 +495,25 @@ typedef struct {
  * well under a second. */
 hb_status hb_measure_ceilings(void *buffer, uint64_t buffer_bytes, hb_ceilings *out, void *stream);
 
+/* ---------------- pinned host buffers (host <-> device copies) ---------------- */
+
+/*
+ * Page-locked host memory for the vectors a caller streams to and from the
+ * device (the end-to-end path of the Lanczos step copies v in every step).
+ * The buffer is an anonymous mapping of `bytes` rounded up to 2 MiB, advised
+ * for transparent huge pages, zero-filled, and registered with the CUDA driver
+ * (cudaHostRegister), so copies run at the link's full rate whichever pages the
+ * host chose.  *ptr is aligned to the host's transparent huge page size (at
+ * least 2 MiB).  Owned by the caller: release it with
+ * hb_host_free.  Errors: HB_ERR_INVALID_ARG (bytes == 0 or ptr null),
+ * HB_ERR_NO_MEMORY (the mapping failed), HB_ERR_CUDA (registration failed;
+ * nothing is left allocated).  Needs a CUDA device for the registration.
+ */
+hb_status hb_host_alloc(uint64_t bytes, void **ptr);
+/* Unregisters and unmaps a buffer from hb_host_alloc (null: no-op).
+ * HB_ERR_INVALID_ARG for any other pointer. */
+hb_status hb_host_free(void *ptr);
+
 /*
  * Host utility (no GPU needed): lowest eigenvalue theta of the symmetric
  * tridiagonal matrix with diagonal alpha[0..n) and off-diagonal beta[0..n-1),

@@ -13,7 +13,7 @@ from ._binding import (HB_F32, HB_F64, HB_FX64, Batch, Handle, Inversion, Mlp, m
                        hubbard_row_entries, hubbard_set_U, lanczos_ground_state, lanczos_ritz_vector_f32, lanczos_step,
                        lanczos_step_noalloc, lanczos_step_scratch_bytes, load, paradeisos_rank, paradeisos_unrank,
                        lanczos_ritz_vector_f64, hubbard_apply_c, hb_continued_fraction, hb_measure_ceilings,
-                       hubbard_apply_timed)
+                       hubbard_apply_timed, host_empty)
 
 EXPORTED_SYMBOLS = ("hb_status_string", "hubbard_basis_create", "hubbard_basis_create_k", "hubbard_basis_destroy",
                     "hubbard_basis_dim",
@@ -27,7 +27,8 @@ EXPORTED_SYMBOLS = ("hb_status_string", "hubbard_basis_create", "hubbard_basis_c
                     "lanczos_batch_workspace_bytes", "lanczos_batch_ground_state", "lanczos_batch_wait_selftest", "paradeisos_inv_create",
                     "paradeisos_inv_destroy", "paradeisos_inv_dim", "paradeisos_inv_rank", "paradeisos_inv_unrank",
                     "paradeisos_inv_last_error", "lanczos_ritz_vector_f64", "hubbard_apply_c",
-                    "hb_continued_fraction", "hb_measure_ceilings", "hubbard_apply_timed")
+                    "hb_continued_fraction", "hb_measure_ceilings", "hubbard_apply_timed", "hb_host_alloc",
+                    "hb_host_free")
 MLP_SYMBOLS = ("mlp_create", "mlp_destroy", "mlp_param_count", "mlp_get_params", "mlp_set_params", "mlp_forward",
                "mlp_gradient", "mlp_adam_step", "mlp_start_vector", "mlp_last_error", "mlp_tc_gemm", "mlp_activation", "mlp_sample_workspace_bytes", "mlp_sample_training",
                "hb_device_wait_selftest")

@@ -141,6 +141,8 @@ def load():
         "lanczos_step_noalloc": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
         "hb_measure_ceilings": (ctypes.c_int, [P, U64, ctypes.POINTER(Ceilings), P]),
         "hubbard_apply_timed": (ctypes.c_int, [P, I32, P, P, P, P, P, P]),
+        "hb_host_alloc": (ctypes.c_int, [U64, ctypes.POINTER(P)]),
+        "hb_host_free": (ctypes.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -800,6 +802,22 @@ def hb_continued_fraction(alphas, betas, norm2: float, E0: float, z):
                                         float(norm2), float(E0), P(zr.ctypes.data), P(zi.ctypes.data), len(z),
                                         P(gr.ctypes.data), P(gi.ctypes.data)), "hb_continued_fraction")
     return gr + 1j * gi
+
+
+def host_empty(n: int, dtype):
+    """A pinned host tensor of n elements on huge pages (hb_host_alloc); the buffer is released
+    (hb_host_free) when the tensor and all its views are gone."""
+    import torch
+    import weakref
+    esize = torch.empty(0, dtype=dtype).element_size()
+    nbytes = max(1, int(n)) * esize
+    torch.cuda.init()  # torch's view of the context: is_pinned() and async copies see the registration
+    lib = load()
+    p = ctypes.c_void_p()
+    _check(lib.hb_host_alloc(nbytes, ctypes.byref(p)), "hb_host_alloc")
+    buf = (ctypes.c_char * nbytes).from_address(p.value)
+    weakref.finalize(buf, lib.hb_host_free, ctypes.c_void_p(p.value))
+    return torch.frombuffer(buf, dtype=dtype, count=int(n))
 
 
 def hb_measure_ceilings(buffer, stream=None) -> dict:

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUTDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUTDIR, "libparadeisos.so")
-SOURCES = ["pd_basis.cu", "pd_hv.cu", "pd_lanczos.cu", "pd_batch.cu", "pd_mlp.cu", "pd_kspace.cu", "pd_inversion.cu", "pd_probe.cu"]
+SOURCES = ["pd_basis.cu", "pd_hv.cu", "pd_lanczos.cu", "pd_batch.cu", "pd_mlp.cu", "pd_kspace.cu", "pd_inversion.cu", "pd_probe.cu", "pd_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

@@ -111,3 +111,15 @@ def test_continued_fraction_matches_oracle(lib):
         got = pd.hb_continued_fraction(a, b, 0.7, -1.3, z)
         want = R.continued_fraction(a, b, 0.7, -1.3, z)
         assert np.max(np.abs(got - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
+
+
+def test_host_alloc_argument_errors(lib):
+    """The pinned-buffer entry points refuse bad arguments before touching the driver."""
+    import ctypes
+    p = ctypes.c_void_p()
+    assert lib.hb_host_alloc(0, ctypes.byref(p)) == 1  # HB_ERR_INVALID_ARG
+    assert p.value is None
+    assert lib.hb_host_alloc(4096, None) == 1
+    assert lib.hb_host_free(None) == 0
+    x = ctypes.create_string_buffer(64)
+    assert lib.hb_host_free(ctypes.cast(x, ctypes.c_void_p)) == 1  # not one of its buffers
