@@ -7,8 +7,9 @@
  * occupation bits of a combined basis state (bit i of (up << L) | dn, the
  * layout of Sec. III) to (log|psi|, sign logit):
  *     z1 = W1 x + b1, a1 = gelu(z1), z2 = W2 a1 + b2, a2 = gelu(z2), out = W3 a2 + b3,
- * hidden width 128, gelu the exact erf form (erf evaluated by Abramowitz &
- * Stegun 7.1.28, |error| <= 3e-7, far below the bfloat16 rounding of the
+ * hidden width 128, gelu the tanh form x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715
+ * x^3))) (Hendrycks & Gimpel 2016), tanh by the hardware's tanh.approx.f32
+ * (relative error about 2^-11, below the bfloat16 rounding of the
  * activations).  Parameters are one float32
  * vector in the order W1 [128 x n_in] row-major, b1 [128], W2 [128 x 128],
  * b2 [128], W3 [2 x 128], b3 [2]; matrix products run on the tensor cores
@@ -65,7 +66,8 @@ hb_status mlp_last_error(hb_mlp_handle m);
 hb_status mlp_tc_gemm(const void *A, const void *B, float *C, int M, int N, int K, void *stream);
 
 /* Test entry: y[i] = gelu(x[i]) (deriv 0) or gelu'(x[i]) (deriv 1), the activation exactly as the
- * network's kernels evaluate it (erf by Abramowitz & Stegun 7.1.28, |error| <= 3e-7).  Asynchronous. */
+ * network's kernels evaluate it (the tanh form above; the derivative is that form's exact
+ * derivative).  Asynchronous. */
 hb_status mlp_activation(const float *x, uint64_t n, float *y, int32_t deriv, void *stream);
 
 /* Failure-detection self test (synchronous): a kernel waits, with the bounded

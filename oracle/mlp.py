@@ -6,7 +6,8 @@ L..2L-1, the combined-integer layout of Sec. III) to (log|psi|, sign logit):
 
     z1 = W1 x + b1,  a1 = gelu(z1),  z2 = W2 a1 + b2,  a2 = gelu(z2),  out = W3 a2 + b3
 
-with gelu the exact erf form (Hendrycks & Gimpel).  The GPU stores weights in
+with gelu in its tanh form, gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
+(Hendrycks & Gimpel, "Gaussian Error Linear Units", 2016).  The GPU stores weights in
 bfloat16 and accumulates in float32; this oracle evaluates in float64 with the
 same quantities rounded to bfloat16 where the GPU rounds them (weights W1, W2,
 W3 and the hidden activation a1 fed to the second matrix product), bfloat16
@@ -22,12 +23,8 @@ import math
 
 import numpy as np
 
-try:
-    from scipy.special import erf as _erf
-except Exception:  # pragma: no cover
-    _erf = np.vectorize(math.erf)
-
-SQRT2 = math.sqrt(2.0)
+SQRT_2_OVER_PI = math.sqrt(2.0 / math.pi)
+GELU_CUBIC = 0.044715
 
 
 def bf16(a: np.ndarray) -> np.ndarray:
@@ -43,11 +40,14 @@ def bf16(a: np.ndarray) -> np.ndarray:
 
 
 def gelu(x):
-    return 0.5 * x * (1.0 + _erf(x / SQRT2))
+    """The tanh form of GELU (the network's activation)."""
+    return 0.5 * x * (1.0 + np.tanh(SQRT_2_OVER_PI * (x + GELU_CUBIC * x ** 3)))
 
 
 def gelu_grad(x):
-    return 0.5 * (1.0 + _erf(x / SQRT2)) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    """d gelu / dx of the same form."""
+    th = np.tanh(SQRT_2_OVER_PI * (x + GELU_CUBIC * x ** 3))
+    return 0.5 * (1.0 + th) + 0.5 * x * (1.0 - th * th) * SQRT_2_OVER_PI * (1.0 + 3.0 * GELU_CUBIC * x * x)
 
 
 def bits_of(states: np.ndarray, L: int) -> np.ndarray:

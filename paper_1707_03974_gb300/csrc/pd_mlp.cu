@@ -3,8 +3,8 @@
 // re-uses the method's own ground states as training data).
 //
 //   z1 = W1 x + b1, a1 = gelu(z1), z2 = W2 a1 + b2, a2 = gelu(z2), out = W3 a2 + b3
-//   out = (log|psi|, sign logit),  hidden width 128, gelu in the exact erf form
-//   (erf evaluated by Abramowitz & Stegun 7.1.28, |error| <= 3e-7).
+//   out = (log|psi|, sign logit),  hidden width 128, gelu in its tanh form
+//   (Hendrycks & Gimpel 2016; tanh by the hardware's tanh.approx.f32).
 //
 // Weights are kept in float32 (master copy, Adam) and used as bfloat16; the two
 // 128-wide matrix products of the forward pass, and the activation-gradient and
@@ -158,30 +158,67 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const __nv_bfloat16 *__restrict
 // ---------------------------------------------------------------------------
 // element-wise kernels
 
-// erf(x) by formula 7.1.28 of Abramowitz & Stegun, Handbook of Mathematical
-// Functions (1964): for x >= 0, erf(x) = 1 - (1 + a1 x + ... + a6 x^6)^-16 with
-// |error| <= 3e-7, odd in x.  The argument is clamped at 6, where erf is 1 to
-// float32 precision, so the power never overflows.  One reciprocal and about
-// thirteen float32 operations: the GELU of the network stays the exact-erf
-// form to far inside bfloat16 resolution (2^-8 relative) at a fraction of the
-// cost of erff.
-__device__ __forceinline__ float erf_as7128(float x) {
-    const float ax = fminf(fabsf(x), 6.0f);
-    float p = fmaf(ax, 0.0000430638f, 0.0002765672f);
-    p = fmaf(ax, p, 0.0001520143f);
-    p = fmaf(ax, p, 0.0092705272f);
-    p = fmaf(ax, p, 0.0422820123f);
-    p = fmaf(ax, p, 0.0705230784f);
-    p = fmaf(ax, p, 1.0f);
-    p = p * p;  // ^2
-    p = p * p;  // ^4
-    p = p * p;  // ^8
-    p = p * p;  // ^16
-    return copysignf(1.0f - __fdividef(1.0f, p), x);
+// GELU in its tanh form (Hendrycks & Gimpel, "Gaussian Error Linear Units",
+// 2016):  gelu(x) = x/2 (1 + tanh(u)),  u = sqrt(2/pi) (x + 0.044715 x^3),
+// with tanh from the SM's tanh.approx.f32 instruction (relative error about
+// 2^-11, far inside the bfloat16 rounding, 2^-9 relative, that every
+// activation then goes through).  Four float32 operations and one
+// special-function instruction per activation.  The derivative is the exact
+// derivative of the same form:
+//   gelu'(x) = (1 + tanh u)/2 + x/2 (1 - tanh^2 u) sqrt(2/pi) (1 + 3 * 0.044715 x^2).
+constexpr float kGeluC1 = 0.7978845608f;   // sqrt(2/pi)
+constexpr float kGeluC3 = 0.0356774081f;   // 0.044715 sqrt(2/pi)
+constexpr float kGeluD3 = 0.1070322244f;   // 3 * 0.044715 sqrt(2/pi)
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erf_as7128(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_f(float x) {
+    const float hx = 0.5f * x;
+    return fmaf(hx, tanh_hw(x * fmaf(kGeluC3, x * x, kGeluC1)), hx);
+}
+// Blackwell's paired float32 instructions (fma/mul/add .rn.f32x2): two float32
+// operations per instruction, each half rounded exactly as the scalar
+// instruction rounds it.  A pair lives in one 64-bit register.
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// gelu of both halves, each bit for bit gelu_f (the same operations in the same order)
+__device__ __forceinline__ unsigned long long gelu_f2(unsigned long long x) {
+    const unsigned long long u =
+        f2_mul(x, f2_fma(f2_pack(kGeluC3, kGeluC3), f2_mul(x, x), f2_pack(kGeluC1, kGeluC1)));
+    const float2 uu = f2_unpack(u);
+    const unsigned long long hx = f2_mul(f2_pack(0.5f, 0.5f), x);
+    return f2_fma(hx, f2_pack(tanh_hw(uu.x), tanh_hw(uu.y)), hx);
+}
 __device__ __forceinline__ float gelu_grad_f(float x) {
-    return 0.5f * (1.0f + erf_as7128(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+    const float x2 = x * x;
+    const float th = tanh_hw(x * fmaf(kGeluC3, x2, kGeluC1));
+    return fmaf(0.5f * x * fmaf(-th, th, 1.0f), fmaf(kGeluD3, x2, kGeluC1), 0.5f * (1.0f + th));
 }
 
 // y = gelu(x) (deriv 0) or gelu'(x) (deriv 1): the activation as the network's kernels evaluate it
@@ -379,12 +416,19 @@ struct InferSmem {
     uint8_t X[kBM * kIn * 2];  // A operand of layer 1
     uint8_t A1[kBM * kH * 2];  // A operand of layer 2
     float b1[kH], b2[kH], w3[2 * kH], b3[2];
+    float red[2][kBM];  // output-layer partial sums of the second column half
     uint64_t bar;
     uint32_t tmem;
 };
 
+// Threads of the fused start-vector kernel: two warpgroups.  Warp w reads the
+// tensor-memory lanes 32 (w mod 4) .. + 31 (the rows of its quarter of the tile)
+// and takes the hidden columns of half w / 4, so each row's 128 columns are
+// split over two warps and each SM keeps twice as many warps on the epilogues.
+constexpr int kStartThreads = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_mlp_start(const __nv_bfloat16 *__restrict__ W1b,
+__global__ void __launch_bounds__(kStartThreads) k_mlp_start(const __nv_bfloat16 *__restrict__ W1b,
                                                    const __nv_bfloat16 *__restrict__ W2b,
                                                    const float *__restrict__ params, uint64_t ob1, uint64_t ob2,
                                                    uint64_t oW3, uint64_t ob3, const uint32_t *__restrict__ str_up,
@@ -393,19 +437,21 @@ __global__ void __launch_bounds__(128) k_mlp_start(const __nv_bfloat16 *__restri
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (kBM - 1), half = tid / kBM;  // tile row of this thread, hidden-column half
     constexpr uint32_t kSBO1 = (kIn / 8) * 128, kSBO2 = (kH / 8) * 128;
+    constexpr int kHalfCols = kH / 2;
     // weights and biases, once per CTA
-    for (int c = tid; c < kH * (kIn / 8); c += 128) {
+    for (int c = tid; c < kH * (kIn / 8); c += kStartThreads) {
         const int r = c / (kIn / 8), kc = c % (kIn / 8);
         *reinterpret_cast<uint4 *>(S.W1 + tc::core_off(r, kc * 8, kSBO1)) =
             *reinterpret_cast<const uint4 *>(W1b + (size_t)r * kIn + kc * 8);
     }
-    for (int c = tid; c < kH * (kH / 8); c += 128) {
+    for (int c = tid; c < kH * (kH / 8); c += kStartThreads) {
         const int r = c / (kH / 8), kc = c % (kH / 8);
         *reinterpret_cast<uint4 *>(S.W2 + tc::core_off(r, kc * 8, kSBO2)) =
             *reinterpret_cast<const uint4 *>(W2b + (size_t)r * kH + kc * 8);
     }
-    for (int i = tid; i < kH; i += 128) {
+    for (int i = tid; i < kH; i += kStartThreads) {
         S.b1[i] = params[ob1 + i];
         S.b2[i] = params[ob2 + i];
         S.w3[i] = __bfloat162float(__float2bfloat16_rn(params[oW3 + i]));
@@ -418,21 +464,23 @@ __global__ void __launch_bounds__(128) k_mlp_start(const __nv_bfloat16 *__restri
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = S.tmem;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     uint32_t phase = 0;
     bool ok = true;
     const uint64_t ntiles = (D + kBM - 1) / kBM;
     for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int t = tid;
+        const int t = row;
         const uint64_t I = tile * kBM + t;
-        // row t of X: the occupation bits of basis state I (zero rows past the end)
+        // row t of X: the occupation bits of basis state I (zero rows past the end), built by the
+        // first warpgroup
         uint64_t state = 0;
-        if (I < D) {
+        if (half == 0 && I < D) {
             const uint64_t u = I / D_dn, d = I - u * D_dn;
             state = ((uint64_t)str_up[u] << L) | (uint64_t)str_dn[d];
         }
 #pragma unroll
         for (int q = 0; q < kIn / 8; ++q) {
+            if (half != 0) break;
             uint32_t w4[4];
 #pragma unroll
             for (int p2 = 0; p2 < 4; ++p2) {
@@ -460,9 +508,9 @@ __global__ void __launch_bounds__(128) k_mlp_start(const __nv_bfloat16 *__restri
         if (!ok) break;
         phase ^= 1;
         tc::fence_after_sync();
-        // epilogue 1: A1[t, :] = bf16(gelu(Z1[t, :] + b1))
+        // epilogue 1: A1[t, :] = bf16(gelu(Z1[t, :] + b1)), this thread's column half
 #pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+        for (int c0 = half * kHalfCols; c0 < (half + 1) * kHalfCols; c0 += 32) {
             float z[32];
             tc::tmem_ld32(tmem + lane_base + (uint32_t)c0, z);
 #pragma unroll
@@ -471,8 +519,10 @@ __global__ void __launch_bounds__(128) k_mlp_start(const __nv_bfloat16 *__restri
 #pragma unroll
                 for (int p2 = 0; p2 < 4; ++p2) {
                     const int i = q * 8 + 2 * p2;
-                    const __nv_bfloat16 a = __float2bfloat16_rn(gelu_f(z[i] + S.b1[c0 + i]));
-                    const __nv_bfloat16 b = __float2bfloat16_rn(gelu_f(z[i + 1] + S.b1[c0 + i + 1]));
+                    const float2 g = f2_unpack(gelu_f2(
+                        f2_add(f2_pack(z[i], z[i + 1]), *reinterpret_cast<const unsigned long long *>(S.b1 + c0 + i))));
+                    const __nv_bfloat16 a = __float2bfloat16_rn(g.x);
+                    const __nv_bfloat16 b = __float2bfloat16_rn(g.y);
                     w4[p2] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
                 }
                 *reinterpret_cast<uint4 *>(S.A1 + tc::core_off(t, c0 + q * 8, kSBO2)) =
@@ -496,21 +546,33 @@ __global__ void __launch_bounds__(128) k_mlp_start(const __nv_bfloat16 *__restri
         if (!ok) break;
         phase ^= 1;
         tc::fence_after_sync();
-        // epilogue 2: output layer (W3 at bf16 precision, as mlp_forward) and the start value
-        float o0 = S.b3[0], o1 = S.b3[1];
+        // epilogue 2: output layer (W3 at bf16 precision, as mlp_forward) and the start value;
+        // paired instructions: even and odd hidden units sum in the two halves of a register
+        unsigned long long p0 = 0ull, p1 = 0ull;  // (+0.0f, +0.0f)
 #pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+        for (int c0 = half * kHalfCols; c0 < (half + 1) * kHalfCols; c0 += 32) {
             float z[32];
             tc::tmem_ld32(tmem + lane_base + (uint32_t)(kH + c0), z);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const float a = gelu_f(z[i] + S.b2[c0 + i]);
-                o0 = fmaf(S.w3[c0 + i], a, o0);
-                o1 = fmaf(S.w3[kH + c0 + i], a, o1);
+            for (int i = 0; i < 32; i += 2) {
+                const unsigned long long a = gelu_f2(
+                    f2_add(f2_pack(z[i], z[i + 1]), *reinterpret_cast<const unsigned long long *>(S.b2 + c0 + i)));
+                p0 = f2_fma(*reinterpret_cast<const unsigned long long *>(S.w3 + c0 + i), a, p0);
+                p1 = f2_fma(*reinterpret_cast<const unsigned long long *>(S.w3 + kH + c0 + i), a, p1);
             }
         }
+        const float2 q0 = f2_unpack(p0), q1 = f2_unpack(p1);
+        if (half == 1) {
+            S.red[0][t] = q0.x + q0.y;
+            S.red[1][t] = q1.x + q1.y;
+        }
         tc::fence_before_sync();  // this tile's tensor-memory reads precede the next tile's MMAs
-        if (I < D) v[I] = start_value<T>(o0, o1, F);
+        __syncthreads();
+        if (half == 0 && I < D) {
+            const float o0 = S.b3[0] + ((q0.x + q0.y) + S.red[0][t]);
+            const float o1 = S.b3[1] + ((q1.x + q1.y) + S.red[1][t]);
+            v[I] = start_value<T>(o0, o1, F);
+        }
     }
     if (!ok) {
         // gave up waiting: record it, then drain (bounded) so no MMA still writes the
@@ -974,19 +1036,20 @@ hb_status mlp_start_vector(hb_mlp_handle m, hb_handle h, hb_dtype dt, void *v, v
     const uint64_t ntiles = (h->D + kBM - 1) / kBM;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, 2ull * m->sm_count));
     const int F = h->fx_frac;
+    constexpr int T = kStartThreads;
     if (dt == HB_F32) {
         PD_CUDA(cudaFuncSetAttribute(k_mlp_start<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_mlp_start<float><<<grid, 128, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3, h->up.str,
+        k_mlp_start<float><<<grid, T, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3, h->up.str,
                                                    h->dn.str, h->D_dn, h->D, h->L, m->n_in,
                                                    static_cast<float *>(v), F, m->d_err);
     } else if (dt == HB_F64) {
         PD_CUDA(cudaFuncSetAttribute(k_mlp_start<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_mlp_start<double><<<grid, 128, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3,
+        k_mlp_start<double><<<grid, T, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3,
                                                     h->up.str, h->dn.str, h->D_dn, h->D, h->L, m->n_in,
                                                     static_cast<double *>(v), F, m->d_err);
     } else {
         PD_CUDA(cudaFuncSetAttribute(k_mlp_start<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_mlp_start<int64_t><<<grid, 128, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3,
+        k_mlp_start<int64_t><<<grid, T, smem, st>>>(m->W1b, m->W2b, m->d_p, m->ob1, m->ob2, m->oW3, m->ob3,
                                                      h->up.str, h->dn.str, h->D_dn, h->D, h->L, m->n_in,
                                                      static_cast<int64_t *>(v), F, m->d_err);
     }

@@ -15,8 +15,18 @@ def test_bf16_rounding_matches_torch():
 
 
 def test_gelu_values_and_derivative():
+    """The tanh form of GELU: pinned to the exact erf form x Phi(x) (math.erf, an independent
+    definition), which it approximates to within 5e-4 everywhere (a dropped cubic term or a wrong
+    scale misses by 1e-2 or more); odd part x/2 exactly, so gelu(x) - gelu(-x) = x; gelu -> x
+    and -> 0 far from the origin; the derivative by central differences."""
+    import math
     assert gelu(0.0) == 0.0
-    assert abs(gelu(1.0) - 0.8413447460685429) < 1e-15
+    xs = np.linspace(-12, 12, 24001)
+    exact = np.array([0.5 * v * (1.0 + math.erf(v / math.sqrt(2.0))) for v in xs])
+    dev = np.abs(gelu(xs) - exact)
+    assert dev.max() < 5e-4 and dev.max() > 1e-4  # the approximation's known size, not the erf form itself
+    assert np.max(np.abs(gelu(xs) - gelu(-xs) - xs)) < 1e-12
+    assert abs(gelu(10.0) - 10.0) < 1e-12 and abs(gelu(-10.0)) < 1e-12
     xs = np.linspace(-5, 5, 41)
     h = 1e-6
     fd = (gelu(xs + h) - gelu(xs - h)) / (2 * h)
