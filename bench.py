@@ -396,7 +396,7 @@ def run_ours(args, world, rank, local):
     achieved = bps * D / (hv_ms * 1e-3) / 1e9
     kname = hv_kernel_key(args.dtype, tuned)
     if "K" in wk:  # momentum sector: one row-factorised kernel
-        kname = {"fx64": "k_k_hv_rows<int64>", "f64": "k_k_hv_rows<double>", "f32": "k_k_hv_rows<float>"}[args.dtype]
+        kname = {"fx64": "k_k_hv_rows2<int64>", "f64": "k_k_hv_rows2<double>", "f32": "k_k_hv_rows2<float>"}[args.dtype]
     traffic = ncu_traffic(kname)
     out = {
         "metric": METRIC, "value": round(job_throughput(D, world, ms), 4), "unit": UNIT, "n_gpus": world,
@@ -699,7 +699,7 @@ def measure_kspace(pd, torch, steps: int = 10):
     return {"workload": "hubbard_4x4_tp-0.3_U8_half_filling_momentum_K00", "D": D, "hv_ms": round(hv_ms, 4),
             "step_ms": round(step_ms, 4), "hv_gstates_per_s": round(D / (hv_ms * 1e-3) / 1e9, 3),
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(gbs / peak, 4), "kernel": "k_k_hv_rows<int64>", "bytes_per_state": 16},
+                         "frac": round(gbs / peak, 4), "kernel": "k_k_hv_rows2<int64>", "bytes_per_state": 16},
             "time_to_E0_fx64": {"seconds": round(e0_s, 4), "iterations": r.iterations, "E0": r.E0,
                                 "converged": r.converged}}
 

@@ -55,6 +55,10 @@ struct KSpace {
     uint32_t *dnmov = nullptr;  // per momentum block: [(q-1) nd + slot][len] G(dn') | sign << 31
     uint8_t *dncnt = nullptr;   // per momentum block: [q-1][len]
     uint64_t *mbase = nullptr, *cbase = nullptr;  // [N]
+    // rows paired by down momentum for the two-row H·v: [npairs][2] row indices,
+    // second entry 0xFFFFFFFF for a row left without a partner; rows of length 0 omitted
+    uint32_t *pairs = nullptr;
+    uint32_t npairs = 0;
 };
 
 namespace {
@@ -419,6 +423,116 @@ __global__ void __launch_bounds__(512) k_k_hv_rows(KHv p, const T *__restrict__ 
     }
 }
 
+// Two rows per CTA: rows u0, u1 of equal down momentum K_dn share the column
+// count, the spin-down move lists and their per-column counts, so each move
+// entry is loaded once and gathers t_q of both rows, and the two rows share
+// each q's CTA barrier.  Per row the work and its order are those of
+// k_k_hv_rows (t_q summed over the row's up moves in list order, then every
+// column adds its spin-down moves in list order), so the results are the same
+// values, bit for bit, for every vector type.
+template <typename T, int JM>
+__global__ void __launch_bounds__(512) k_k_hv_rows2(KHv p, const uint32_t *__restrict__ pairs, uint32_t npairs,
+                                                      const T *__restrict__ x, T *__restrict__ y, uint32_t maxlen) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = p.a.N, nu = p.a.nu, nd = p.a.nd;
+    const size_t nup = (size_t)(N - 1) * (nu > 0 ? nu : 1);
+    uint64_t *s_up = reinterpret_cast<uint64_t *>(smem);           // [2][nup]
+    uint8_t *s_cnt = reinterpret_cast<uint8_t *>(s_up + 2 * nup);  // [2][32]
+    // per-q row sums, double-buffered as in k_k_hv_rows: [buffer][row of the pair][maxlen]
+    T *s_t = reinterpret_cast<T *>(smem + ((2 * nup * 8 + 64 + 15) & ~(size_t)15));
+    for (uint32_t pi = blockIdx.x; pi < npairs; pi += gridDim.x) {
+        const uint32_t r0 = pairs[2 * (uint64_t)pi], r1 = pairs[2 * (uint64_t)pi + 1];
+        const bool two = r1 != 0xFFFFFFFFu;
+        const int kd = (int)p.rowKd[r0];
+        const uint32_t len = (uint32_t)(p.doff[kd + 1] - p.doff[kd]);
+        __syncthreads();  // the previous pair is done with shared memory
+        for (int e = threadIdx.x; e < (N - 1) * nu; e += blockDim.x) {
+            s_up[e] = p.upmov[r0 * (uint64_t)(N - 1) * nu + e];
+            s_up[nup + e] = two ? p.upmov[r1 * (uint64_t)(N - 1) * nu + e] : 0ull;
+        }
+        if (threadIdx.x < N - 1) {
+            s_cnt[threadIdx.x] = p.upcnt[r0 * (uint64_t)(N - 1) + threadIdx.x];
+            s_cnt[32 + threadIdx.x] = two ? p.upcnt[r1 * (uint64_t)(N - 1) + threadIdx.x] : (uint8_t)0;
+        }
+        __syncthreads();
+        const uint32_t *dm = p.dnmov + p.mbase[kd];
+        const uint8_t *dc = p.dncnt + p.cbase[kd];
+        int64_t ai0[JM], ai1[JM];
+        T af0[JM], af1[JM];
+#pragma unroll
+        for (int i = 0; i < JM; ++i) ai0[i] = ai1[i] = 0, af0[i] = af1[i] = T(0);
+        int buf = 0;
+        for (int q = 1; q < N; ++q) {
+            const int cu0 = s_cnt[q - 1], cu1 = s_cnt[32 + q - 1];
+            if (cu0 == 0 && cu1 == 0) continue;  // uniform
+            const int kd2 = ksub(p.a.Lx, p.a.Ly, kd, q);
+            const uint32_t len2 = (uint32_t)(p.doff[kd2 + 1] - p.doff[kd2]);
+            const uint64_t *ua0 = s_up + (size_t)(q - 1) * nu, *ua1 = ua0 + nup;
+            T *st0 = s_t + (size_t)buf * 2 * maxlen, *st1 = st0 + maxlen;
+            for (uint32_t e = threadIdx.x; e < len2; e += blockDim.x) {
+                T t0 = T(0), t1 = T(0);
+                for (int a = 0; a < cu0; ++a) {
+                    const uint64_t m = ua0[a];
+                    const T v = x[(m & 0x7FFFFFFFFFFFFFFFull) + e];
+                    t0 = (m >> 63) ? t0 - v : t0 + v;
+                }
+                for (int a = 0; a < cu1; ++a) {
+                    const uint64_t m = ua1[a];
+                    const T v = x[(m & 0x7FFFFFFFFFFFFFFFull) + e];
+                    t1 = (m >> 63) ? t1 - v : t1 + v;
+                }
+                st0[e] = t0;
+                st1[e] = t1;
+            }
+            __syncthreads();
+            const uint8_t *dcq = dc + (uint64_t)(q - 1) * len;
+            const uint32_t *dmq = dm + (uint64_t)(q - 1) * nd * len;
+#pragma unroll
+            for (int i = 0; i < JM; ++i) {
+                const uint32_t j = threadIdx.x + (uint32_t)i * blockDim.x;
+                if (j >= len) break;
+                const int cd = dcq[j];
+                const uint32_t *dmj = dmq + j;
+                for (int b = 0; b < cd; ++b) {
+                    const uint32_t ev = dmj[(uint64_t)b * len];
+                    const uint32_t g = ev & 0x7FFFFFFFu;
+                    const T v0 = st0[g], v1 = st1[g];
+                    if constexpr (std::is_same<T, int64_t>::value) {
+                        const int64_t mneg = -(int64_t)(ev >> 31);
+                        ai0[i] += (v0 ^ mneg) - mneg;
+                        ai1[i] += (v1 ^ mneg) - mneg;
+                    } else {
+                        af0[i] += (ev >> 31) ? -v0 : v0;
+                        af1[i] += (ev >> 31) ? -v1 : v1;
+                    }
+                }
+            }
+            buf ^= 1;
+        }
+        const uint64_t e0 = p.doff[kd];
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            if (w == 1 && !two) break;
+            const uint32_t r = w ? r1 : r0;
+            const uint64_t F = p.rowF[r];
+            const double eur = p.eu[r];
+#pragma unroll
+            for (int i = 0; i < JM; ++i) {
+                const uint32_t j = threadIdx.x + (uint32_t)i * blockDim.x;
+                if (j >= len) break;
+                const double diag = eur + p.ed[e0 + j] + p.U_diag;
+                const T xI = x[F + j];
+                if constexpr (std::is_same<T, int64_t>::value) {
+                    const FxCoef c = fx_coef_dev(diag);
+                    y[F + j] = fx_mul(xI, c.K, c.G) + fx_mul(w ? ai1[i] : ai0[i], p.Kun, p.Gun);
+                } else {
+                    y[F + j] = (T)diag * xI + (T)p.U_over_N * (w ? af1[i] : af0[i]);
+                }
+            }
+        }
+    }
+}
+
 // Batched spin-full maps for the API: states are (up << N) | dn over the momentum bits.
 __global__ void k_k_rank(KArgs a, const uint64_t *__restrict__ states, uint64_t *__restrict__ idx, uint64_t n,
                          unsigned *err) {
@@ -596,6 +710,7 @@ void pd_k_free(KSpace *k) {
     cudaFree(k->Cdn), cudaFree(k->Ct), cudaFree(k->eps), cudaFree(k->ustr), cudaFree(k->rowF), cudaFree(k->rowKd);
     cudaFree(k->eu), cudaFree(k->upmov), cudaFree(k->upcnt), cudaFree(k->doff), cudaFree(k->dstr), cudaFree(k->dkd);
     cudaFree(k->ed), cudaFree(k->dnmov), cudaFree(k->dncnt), cudaFree(k->mbase), cudaFree(k->cbase);
+    cudaFree(k->pairs);
     delete k;
 }
 
@@ -656,6 +771,20 @@ hb_status build_kspace(hb_handle h, KSpace &k) {
                                                            k.dnmov, k.dncnt);
     PD_CUDA(cudaGetLastError());
     PD_CUDA(cudaDeviceSynchronize());
+    // rows paired by down momentum (ascending row order within each momentum) for k_k_hv_rows2
+    std::vector<uint32_t> kd_of(k.Dup);
+    PD_CUDA(cudaMemcpy(kd_of.data(), k.rowKd, k.Dup * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    std::vector<std::vector<uint32_t>> by_kd(N);
+    for (uint64_t r = 0; r < k.Dup; ++r)
+        if (kd_of[r] < (uint32_t)N && k.h_doff[kd_of[r] + 1] > k.h_doff[kd_of[r]]) by_kd[kd_of[r]].push_back((uint32_t)r);
+    std::vector<uint32_t> pairs;
+    for (int kd = 0; kd < N; ++kd)
+        for (size_t i = 0; i < by_kd[kd].size(); i += 2) {
+            pairs.push_back(by_kd[kd][i]);
+            pairs.push_back(i + 1 < by_kd[kd].size() ? by_kd[kd][i + 1] : 0xFFFFFFFFu);
+        }
+    k.npairs = (uint32_t)(pairs.size() / 2);
+    if (!pairs.empty() && (s = upload(&k.pairs, pairs)) != HB_OK) return s;
     return HB_OK;
 }
 
@@ -680,12 +809,33 @@ hb_status launch_rows(hb_handle h, const KHv &p, const T *x, T *y, cudaStream_t 
     return HB_OK;
 }
 
+// Two rows of equal down momentum per CTA (k_k_hv_rows2); block size as in launch_rows.
+template <typename T, int JM>
+hb_status launch_rows2(hb_handle h, const KHv &p, const T *x, T *y, cudaStream_t st, uint64_t maxlen) {
+    const KSpace &k = *h->ks;
+    const size_t nup = (size_t)(k.N - 1) * std::max(k.nu, 1);
+    const size_t smem = ((2 * nup * 8 + 64 + 15) & ~(size_t)15) + 4 * (size_t)maxlen * sizeof(T);
+    const int threads = (int)std::min<uint64_t>(512, std::max<uint64_t>(64, (maxlen + JM * 32 - 1) / (JM * 32) * 32));
+    auto kern = k_k_hv_rows2<T, JM>;
+    PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) return HB_ERR_NO_MEMORY;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(k.npairs, (uint64_t)per_sm * h->sm_count));
+    kern<<<grid, threads, smem, st>>>(p, k.pairs, k.npairs, x, y, (uint32_t)maxlen);
+    PD_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
 template <typename T>
 hb_status k_apply_t(hb_handle h, const T *x, T *y, cudaStream_t st) {
     const KHv p = khv(h);
     uint64_t maxlen = 0;
     for (int k = 0; k < h->ks->N; ++k) maxlen = std::max(maxlen, h->ks->h_doff[k + 1] - h->ks->h_doff[k]);
-    // row-factorised form while a row fits the per-thread accumulators and shared memory
+    // row-factorised form while a row fits the per-thread accumulators and shared memory; rows
+    // in pairs of equal down momentum while both rows' double-buffered sums fit
+    if (maxlen <= 4 * 512 && 4 * maxlen * sizeof(T) <= 96 * 1024 && h->ks->pairs)
+        return launch_rows2<T, 4>(h, p, x, y, st, maxlen);
     if (maxlen <= 4 * 512 && 2 * maxlen * sizeof(T) <= 96 * 1024) return launch_rows<T, 4>(h, p, x, y, st, maxlen);
     if (maxlen <= 16 * 512 && 2 * maxlen * sizeof(T) <= 192 * 1024) return launch_rows<T, 16>(h, p, x, y, st, maxlen);
     constexpr int kWarps = 8;  // pairwise form, one row per warp
