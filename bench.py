@@ -54,9 +54,6 @@ COMMON = {"vector_dtype": "f64",
 METRIC = "H·v Gstates/s (Lanczos step)"
 UNIT = "Gstates/s"
 HV_BYTES_PER_STATE = 16  # float64: read x once, write y once
-# the fixed-point step's first vector pass inside the H·v adds one compulsory read (vprev):
-# v is the H·v's own input and w its output
-FIRST_PASS_EXTRA_BYTES = 8
 MIXED_F32_TOL_EXP = -6  # residual (10^x max(1,|theta|)) at which a kept-basis float32 phase hands over
 
 
@@ -119,13 +116,6 @@ def hv_kernel_key(dtype: str, cfg: dict) -> str:
            "f64": f"{base},false> (row pass)"}[dtype]
     return (f"{row} + " + up.format(r=cfg.get("up_rows") or 1)
             + f" (block {cfg.get('up_block') or 256}, {cfg.get('up_threads') or 1024} threads)")
-
-
-def fused_kernel_key(cfg: dict) -> str:
-    """Name of the two launches of a fixed-point step's H·v with its first vector pass."""
-    rows = cfg.get("rows_per_cta") or 2
-    return (f"k_hv_fx_up<{cfg.get('up_rows') or 1},2> (spin-up term stored, block {cfg.get('up_block') or 256}, "
-            f"{cfg.get('up_threads') or 1024} threads) + k_hv_fx_wb_step<{rows},2> (row pass + first vector pass)")
 
 
 def ncu_traffic(kernel_key: str):
@@ -292,7 +282,6 @@ def run_ours(args, world, rank, local):
 
     # the two passes of the H·v timed separately (events between them), for the on-chip rooflines
     pass_ms = hv_pass_times(pd, h, V[nsteps % 3], V[(nsteps + 1) % 3], torch)
-    fused = args.dtype == "fx64" and "K" not in wk and pd.lanczos_step_fused(h, vdt)
     ceil = measure_ceilings(pd, torch, dev)
 
     # end to end through the public API with host buffers: every step copies its input vector
@@ -416,15 +405,8 @@ def run_ours(args, world, rank, local):
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs") if peaks else 6800.0
     bps = HV_BYTES_PER_STATE if args.dtype != "f32" else 8
+    achieved = bps * D / (hv_ms * 1e-3) / 1e9
     kname = hv_kernel_key(args.dtype, tuned)
-    # the split fixed-point step runs its first vector pass inside the H·v's row pass: the events
-    # inside the step then bracket H·v + that pass, whose compulsory bytes add the vprev read
-    step_hv_ms = hv_ms
-    if fused:
-        bps = HV_BYTES_PER_STATE + FIRST_PASS_EXTRA_BYTES
-        kname = fused_kernel_key(tuned)
-        hv_ms = pass_ms["row_pass_ms"] + pass_ms["up_pass_ms"]  # the plain H·v (hubbard_apply)
-    achieved = bps * D / (step_hv_ms * 1e-3) / 1e9
     if "K" in wk:  # momentum sector: one row-factorised kernel
         kname = {"fx64": "k_k_hv_rows2<int64>", "f64": "k_k_hv_rows2<double>", "f32": "k_k_hv_rows2<float>"}[args.dtype]
     traffic = ncu_traffic(kname)
@@ -440,14 +422,11 @@ def run_ours(args, world, rank, local):
         "config": {**COMMON, **wk, "vector_dtype": args.dtype},
         "hv_ms": round(hv_ms, 4), "hv_gstates_per_s": round(D / (hv_ms * 1e-3) / 1e9, 4),
         "hv_config": tuned,
-        "step_hv_ms": round(step_hv_ms, 4),
-        "step_hv": ("H·v with the step's first vector pass inside its row pass (w = H v - beta vprev and "
-                    "the exact sums <w,v>, <w,w>, <v,v>); hv_ms is the plain H·v" if fused else "the plain H·v"),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      # DRAM bytes the kernels actually move (committed ncu capture) over the same time
-                     "dram_gbs": round(traffic / (step_hv_ms * 1e-3) / 1e9, 1) if traffic else None,
-                     "kernel": kname, "bytes_per_state": bps, "kernel_ms": round(step_hv_ms, 4),
+                     "dram_gbs": round(traffic / (hv_ms * 1e-3) / 1e9, 1) if traffic else None,
+                     "kernel": kname, "bytes_per_state": bps,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "e2e": {"value": round(job_throughput(D, world, e2e_ms), 4), "unit": UNIT,
                 "h2d_bytes_per_step": D * host_bytes, "d2h_bytes_per_step": 16,

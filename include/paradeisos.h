@@ -263,13 +263,7 @@ hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes);
  * 128-bit integers, or float32 pairs with exact products), from which
  * beta^2 = <w,w> - 2 alpha <w,v> + alpha^2 <v,v> is evaluated (double-double /
  * float64 arithmetic); the second writes (w - alpha v) / beta.  HB_F64 keeps the
- * textbook three passes.  Under the split H·v with its warp-blocked spin-down
- * table (lanczos_step_fused reports it), the HB_FX64 step runs the first pass
- * inside the H·v: the spin-up pass stores its term in w, and the row pass, which
- * holds rows of v in shared memory, completes w = H v - beta_prev vprev element
- * by element and accumulates the three exact sums.  The integer operations per
- * element and the exact sums are those of the separate pass, so w, alpha and
- * beta are bit-identical to it.
+ * textbook three passes.
  * dt            element type of v, vprev, w (device vectors of length D; w must not
  *               overlap v or vprev).
  * vprev, beta_prev  previous vector and device scalar; both NULL on the first step.
@@ -277,27 +271,14 @@ hb_status lanczos_step_scratch_bytes(hb_handle h, uint64_t *bytes);
  *               lanczos_ground_state).
  * scratch       caller-owned device buffer of lanczos_step_scratch_bytes bytes.
  * ev_hv_begin, ev_hv_end  optional cudaEvent_t (as void*) recorded on `stream`
- *               just before and just after the H·v kernel (a timing hook; NULL to skip);
- *               for a fused HB_FX64 step they bracket the H·v with its first pass.
+ *               just before and just after the H·v kernel (a timing hook; NULL to skip).
  * launches      optional host counter, incremented by the number of kernels enqueued
- *               (H·v: 1, or 2 in the split form; then 3, or 5 for HB_F64, or 2 for a
- *               fused HB_FX64 step).
+ *               (H·v: 1, or 2 in the split form; then 3, or 5 for HB_F64).
  * Asynchronous on `stream`.
  */
 hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vprev, void *w, const double *beta_prev,
                        double *alpha, double *beta, void *scratch, uint64_t scratch_bytes, void *ev_hv_begin,
                        void *ev_hv_end, uint32_t *launches, void *stream);
-
-/*
- * Whether lanczos_step (and the fixed-point phases of lanczos_ground_state) run
- * the first vector pass of the step inside the H·v for element type dt under the
- * handle's current H·v configuration: *fused = 1 for HB_FX64 in the split form
- * with the warp-blocked spin-down table, else 0.  Builds the handle's tables if
- * they are not built yet (synchronous).  A configuration outside the paper: the
- * fusion changes the order of the kernels of one step (Sec. I's recurrence), not
- * what they compute.
- */
-hb_status lanczos_step_fused(hb_handle h, hb_dtype dt, int *fused);
 
 /*
  * lanczos_step without any allocation (the paper has no counterpart; this is a

@@ -11,7 +11,7 @@ from ._binding import (HB_F32, HB_F64, HB_FX64, Batch, Handle, Inversion, Mlp, m
                        hubbard_fixed_point_bits, hubbard_get_hv_config, hubbard_set_hv_config, HubbardError, LanczosResult, hb_tridiag_lowest,  # noqa: F401
                        hubbard_apply, hubbard_basis_create, hubbard_basis_destroy, hubbard_last_error,
                        hubbard_row_entries, hubbard_set_U, lanczos_ground_state, lanczos_ritz_vector_f32, lanczos_step,
-                       lanczos_step_fused, lanczos_step_noalloc, lanczos_step_scratch_bytes, load, paradeisos_rank, paradeisos_unrank,
+                       lanczos_step_noalloc, lanczos_step_scratch_bytes, load, paradeisos_rank, paradeisos_unrank,
                        lanczos_ritz_vector_f64, hubbard_apply_c, hb_continued_fraction, hb_measure_ceilings,
                        hubbard_apply_timed, host_empty)
 
@@ -19,7 +19,7 @@ EXPORTED_SYMBOLS = ("hb_status_string", "hubbard_basis_create", "hubbard_basis_c
                     "hubbard_basis_dim",
                     "hubbard_set_U", "paradeisos_rank", "paradeisos_unrank", "hubbard_apply", "hubbard_row_entries",
                     "hubbard_last_error", "lanczos_workspace_bytes", "lanczos_ground_state", "hb_tridiag_lowest",
-                    "lanczos_step_scratch_bytes", "lanczos_step", "lanczos_step_fused", "lanczos_step_noalloc",
+                    "lanczos_step_scratch_bytes", "lanczos_step", "lanczos_step_noalloc",
                     "hubbard_fixed_point_bits", "hubbard_convert", "hubbard_get_hv_config",
                     "hubbard_set_hv_config", "hubbard_autotune", "lanczos_ritz_vector_f32", "hubbard_batch_create", "hubbard_batch_destroy",
                     "hubbard_batch_layout", "hubbard_batch_apply", "hubbard_batch_autotune", "hubbard_batch_get_config",

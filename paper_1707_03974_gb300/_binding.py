@@ -139,7 +139,6 @@ def load():
         "lanczos_step_scratch_bytes": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
         "lanczos_step": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, U64, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
         "lanczos_step_noalloc": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint32), P]),
-        "lanczos_step_fused": (ctypes.c_int, [P, I32, ctypes.POINTER(ctypes.c_int)]),
         "hb_measure_ceilings": (ctypes.c_int, [P, U64, ctypes.POINTER(Ceilings), P]),
         "hubbard_apply_timed": (ctypes.c_int, [P, I32, P, P, P, P, P, P]),
         "hb_host_alloc": (ctypes.c_int, [U64, ctypes.POINTER(P)]),
@@ -444,13 +443,6 @@ def lanczos_step(h: Handle, v, vprev, w, beta_prev, alpha, beta, scratch, ev_hv_
                                _ptr(scratch), scratch.numel() * scratch.element_size(), ev0, ev1,
                                ctypes.byref(launches) if launches is not None else None, _stream_ptr(stream)),
            "lanczos_step")
-
-
-def lanczos_step_fused(h: Handle, dtype) -> bool:
-    """Whether the step of this element type runs its first vector pass inside the H·v."""
-    f = ctypes.c_int(0)
-    _check(load().lanczos_step_fused(h.ptr, _dtype_of(dtype), ctypes.byref(f)), "lanczos_step_fused")
-    return bool(f.value)
 
 
 def lanczos_step_noalloc(h: Handle, v, vprev, w, beta_prev, alpha, beta, ev_hv_begin=None, ev_hv_end=None,

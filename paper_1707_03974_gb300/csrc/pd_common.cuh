@@ -111,16 +111,6 @@ hb_status pd_build_tables(hb_handle h);
 hb_status pd_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st);
 // kernels one pd_apply launches under the handle's configuration for dt
 int pd_hv_launches(hb_handle h, hb_dtype dt);
-// Fixed-point Lanczos step with its first vector pass fused into the split H·v
-// (pd_hv.cu): the spin-up pass stores its term in w, then the row pass forms
-// w = H v - beta_prev vprev and writes the exact sums <w,v>, <w,w>, <v,v> of
-// each of its *nb (<= max_blocks) CTAs into partials (three 16-byte integers
-// per CTA, the layout of k_fx_axpy_dot3).  pd_fx_step_fuses says whether the
-// handle's configuration allows it (split form with the warp-blocked table);
-// otherwise pd_fx_step_hv returns HB_ERR_INVALID_STATE and launches nothing.
-bool pd_fx_step_fuses(hb_handle h);
-hb_status pd_fx_step_hv(hb_handle h, const int64_t *v, const int64_t *vprev, const double *beta_prev, int64_t *w,
-                        void *partials, int max_blocks, int *nb, cudaStream_t st);
 void pd_record_error(hb_handle h, hb_status s);
 // momentum-space counterparts (pd_kspace.cu)
 hb_status pd_k_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_t st);

@@ -17,7 +17,6 @@
 // R rows do not fit in shared memory the down gathers read global memory.
 #include <algorithm>
 
-#include "pd_exact.cuh"
 #include "pd_hv_body.cuh"
 #include "pd_hv_f32wb.cuh"
 
@@ -289,7 +288,7 @@ hb_status launch_hv_fx_wb(hb_handle h, const FxArgs &a, const int64_t *x, int64_
     return launch_hv_fx_wb_lb<R, NC, 1024>(h, a, x, y, st, threads);
 }
 
-template <int RR, int NC, bool IDX32, int LB, int V, bool ASSIGN = false>
+template <int RR, int NC, bool IDX32, int LB, int V>
 __global__ void __launch_bounds__(LB) k_hv_fx_up(const FxArgs a, const int64_t *__restrict__ x,
                                                    int64_t *__restrict__ y, int W, uint64_t n_groups,
                                                    uint64_t n_items) {
@@ -297,67 +296,7 @@ __global__ void __launch_bounds__(LB) k_hv_fx_up(const FxArgs a, const int64_t *
     const int S = blockDim.x / W;
     ItemWalk w(n_groups);
     for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x, w.next())
-        hv_fx_up_item<RR, NC, IDX32, V, void, ASSIGN>(a, x, y, w.j, w.g, W, S, smem);
-}
-
-// ---------------------------------------------------------------------------
-// Fixed-point Lanczos step with its first vector pass fused into the H·v.
-// The spin-up pass runs first and stores its term alone in w (ASSIGN); the row
-// pass then forms, per element, w = [row pass] + [spin-up term] - beta_prev
-// vprev (the same integer operations as k_fx_axpy_dot3, so w is bit-identical)
-// and the exact 128-bit sums <w, v>, <w, w>, <v, v>, taking v from the rows it
-// has staged in shared memory.  Per CTA the three sums go to
-// partials[blockIdx.x], [gridDim.x + blockIdx.x], [2 gridDim.x + blockIdx.x].
-template <int R>
-struct FxStepEpi {
-    int64_t *w;
-    const int64_t *vprev;  // null on the first step
-    int64_t bK;
-    int bG;
-    pdx::I128 swv, sww, svv;
-    int64_t yu[R], pv[R];
-    __device__ __forceinline__ void load(const uint64_t *ur, int nr, uint64_t Dd, uint32_t col) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (r >= nr) continue;
-            yu[r] = w[ur[r] * Dd + col];
-            pv[r] = vprev ? vprev[ur[r] * Dd + col] : 0;
-        }
-    }
-    __device__ __forceinline__ void put(int r, uint64_t i, int64_t row_term, int64_t v) {
-        int64_t o = (int64_t)((uint64_t)row_term + (uint64_t)yu[r]);
-        if (vprev) o -= fx_mul(pv[r], bK, bG);
-        w[i] = o;
-        pdx::i128_add_prod(swv, o, v);
-        pdx::i128_add_prod(sww, o, o);
-        pdx::i128_add_prod(svv, v, v);
-    }
-    __device__ __forceinline__ void block_done() {}
-};
-
-template <int R, int NC, int LB>
-__global__ void __launch_bounds__(LB) k_hv_fx_wb_step(const FxArgs a, const int64_t *__restrict__ v,
-                                                      int64_t *__restrict__ w, const int64_t *__restrict__ vprev,
-                                                      const double *__restrict__ beta_prev,
-                                                      pdx::I128 *__restrict__ partials) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    hv_fx_load_diag(a, smem);
-    FxStepEpi<R> e;
-    e.w = w;
-    e.vprev = vprev;
-    const FxCoef b = vprev ? fx_coef_dev(*beta_prev) : FxCoef();
-    e.bK = b.K;
-    e.bG = b.G;
-    const uint64_t ngroups = (a.Du + R - 1) / R;
-    for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) hv_fx_wb_group<R, NC>(a, v, w, g, smem, &e);
-    const pdx::I128 s0 = pdx::block_sum128(e.swv);
-    const pdx::I128 s1 = pdx::block_sum128(e.sww);
-    const pdx::I128 s2 = pdx::block_sum128(e.svv);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = s0;
-        partials[gridDim.x + blockIdx.x] = s1;
-        partials[2 * gridDim.x + blockIdx.x] = s2;
-    }
+        hv_fx_up_item<RR, NC, IDX32, V>(a, x, y, w.j, w.g, W, S, smem);
 }
 
 template <int R, int NC, bool SMEM, int LB, bool DO_A>
@@ -378,13 +317,13 @@ hb_status launch_hv_fx(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *
     return launch_hv_fx_lb<R, NC, SMEM, 1024, DO_A>(h, a, x, y, st, threads);
 }
 
-template <int RR, int NC, bool IDX32, int V, bool ASSIGN = false>
+template <int RR, int NC, bool IDX32, int V>
 hb_status launch_fx_up_v(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st,
                          const UpShape &u) {
     const int RA = u.S * RR, threads = u.W * u.S;
     const size_t smem = hv_fx_up_smem_bytes<IDX32>(RA, a.zmax_up);
     const uint64_t n_groups = (a.Du + RA - 1) / RA, n_items = (a.Dd + (uint64_t)u.W * V - 1) / ((uint64_t)u.W * V) * n_groups;
-    auto kern = threads <= 512 ? k_hv_fx_up<RR, NC, IDX32, 512, V, ASSIGN> : k_hv_fx_up<RR, NC, IDX32, 1024, V, ASSIGN>;
+    auto kern = threads <= 512 ? k_hv_fx_up<RR, NC, IDX32, 512, V> : k_hv_fx_up<RR, NC, IDX32, 1024, V>;
     unsigned grid = 0;
     hb_status s = persistent_launch_dims(h, kern, threads, smem, n_items, &grid);
     if (s != HB_OK) return s;
@@ -393,68 +332,11 @@ hb_status launch_fx_up_v(hb_handle h, const FxArgs &a, const int64_t *x, int64_t
     return HB_OK;
 }
 
-template <int RR, int NC, bool IDX32, bool ASSIGN = false>
+template <int RR, int NC, bool IDX32>
 hb_status launch_fx_up(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st,
                        const UpShape &u) {
-    return up_pairs<int64_t>(a.Dd, x, y) ? launch_fx_up_v<RR, NC, IDX32, 2, ASSIGN>(h, a, x, y, st, u)
-                                         : launch_fx_up_v<RR, NC, IDX32, 1, ASSIGN>(h, a, x, y, st, u);
-}
-
-template <int NC, bool ASSIGN>
-hb_status fx_up_pass(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y, cudaStream_t st,
-                     const HvConfig &cfg) {
-    const UpShape u = up_shape(cfg, a.Dd);
-    if (h->D < (1ull << 32)) {
-        if (u.RR == 4) return launch_fx_up<4, NC, true, ASSIGN>(h, a, x, y, st, u);
-        return u.RR == 2 ? launch_fx_up<2, NC, true, ASSIGN>(h, a, x, y, st, u)
-                         : launch_fx_up<1, NC, true, ASSIGN>(h, a, x, y, st, u);
-    }
-    if (u.RR == 4) return launch_fx_up<4, NC, false, ASSIGN>(h, a, x, y, st, u);
-    return u.RR == 2 ? launch_fx_up<2, NC, false, ASSIGN>(h, a, x, y, st, u)
-                     : launch_fx_up<1, NC, false, ASSIGN>(h, a, x, y, st, u);
-}
-
-// Rows staged per CTA by the warp-blocked fixed-point row pass under cfg (0: that
-// pass does not run, i.e. the one-kernel form or no warp-blocked table).
-int fx_wb_rows(const FxArgs &a, const HvConfig &cfg, size_t budget, size_t extra = 0) {
-    if (a.wb_nblk == 0) return 0;
-    auto fits_wb = [&](int R) { return hv_fx_wb_smem_bytes(R, a.Dd) + extra <= budget; };
-    int R = cfg.rows == 1 ? 1 : 2;
-    if (!fits_wb(R)) R = 1;
-    return fits_wb(R) ? R : 0;
-}
-
-template <int R, int NC, int LB>
-hb_status launch_fx_wb_step_lb(hb_handle h, const FxArgs &a, const int64_t *v, int64_t *w, const int64_t *vprev,
-                               const double *beta_prev, pdx::I128 *partials, int max_blocks, int *nb,
-                               cudaStream_t st, int threads) {
-    auto kern = k_hv_fx_wb_step<R, NC, LB>;
-    const size_t smem = hv_fx_wb_smem_bytes(R, a.Dd);
-    unsigned grid = 0;
-    hb_status s = persistent_launch_dims(h, kern, threads, smem, (a.Du + R - 1) / R, &grid);
-    if (s != HB_OK) return s;
-    grid = std::min<unsigned>(grid, (unsigned)max_blocks);
-    kern<<<grid, threads, smem, st>>>(a, v, w, vprev, beta_prev, partials);
-    PD_CUDA(cudaGetLastError());
-    *nb = (int)grid;
-    return HB_OK;
-}
-
-template <int NC>
-hb_status fx_step_nc(hb_handle h, const FxArgs &a, const int64_t *v, int64_t *w, const int64_t *vprev,
-                     const double *beta_prev, pdx::I128 *partials, int max_blocks, int *nb, cudaStream_t st,
-                     const HvConfig &cfg, int R) {
-    hb_status s = fx_up_pass<NC, true>(h, a, v, w, st, cfg);
-    if (s != HB_OK) return s;
-    const int threads = pick_threads(cfg, a.Dd);
-    if (R == 2)
-        return threads <= 512
-                   ? launch_fx_wb_step_lb<2, NC, 512>(h, a, v, w, vprev, beta_prev, partials, max_blocks, nb, st, threads)
-                   : launch_fx_wb_step_lb<2, NC, 1024>(h, a, v, w, vprev, beta_prev, partials, max_blocks, nb, st,
-                                                       threads);
-    return threads <= 512
-               ? launch_fx_wb_step_lb<1, NC, 512>(h, a, v, w, vprev, beta_prev, partials, max_blocks, nb, st, threads)
-               : launch_fx_wb_step_lb<1, NC, 1024>(h, a, v, w, vprev, beta_prev, partials, max_blocks, nb, st, threads);
+    return up_pairs<int64_t>(a.Dd, x, y) ? launch_fx_up_v<RR, NC, IDX32, 2>(h, a, x, y, st, u)
+                                         : launch_fx_up_v<RR, NC, IDX32, 1>(h, a, x, y, st, u);
 }
 
 template <int NC, bool DO_A>
@@ -495,8 +377,9 @@ hb_status apply_fx_nc(hb_handle h, const FxArgs &a, const int64_t *x, int64_t *y
     return u.RR == 2 ? launch_fx_up<2, NC, false>(h, a, x, y, st, u) : launch_fx_up<1, NC, false>(h, a, x, y, st, u);
 }
 
-// The fixed-point kernel arguments of handle h, and the shared-memory budget per CTA.
-hb_status make_fx_args(hb_handle h, FxArgs &a, size_t *budget) {
+hb_status apply_fx(hb_handle h, const int64_t *x, int64_t *y, cudaStream_t st, int part) {
+    if (!h->fx_ok) return HB_ERR_INVALID_ARG;
+    FxArgs a;
     a.Du = h->D_up;
     a.Dd = h->D_dn;
     a.str_up = h->up.str;
@@ -529,17 +412,7 @@ hb_status make_fx_args(hb_handle h, FxArgs &a, size_t *budget) {
     }
     int max_smem = 0;
     PD_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    *budget = (size_t)max_smem;
-    return HB_OK;
-}
-
-hb_status apply_fx(hb_handle h, const int64_t *x, int64_t *y, cudaStream_t st, int part) {
-    if (!h->fx_ok) return HB_ERR_INVALID_ARG;
-    FxArgs a;
-    size_t budget = 0;
-    hb_status s = make_fx_args(h, a, &budget);
-    if (s != HB_OK) return s;
-    const HvConfig &cfg = h->hv_cfg[HB_FX64];
+    const size_t budget = (size_t)max_smem;
     switch (std::max(1, h->n_classes)) {
         case 1: return apply_fx_nc<1>(h, a, x, y, st, budget, cfg, part);
         case 2: return apply_fx_nc<2>(h, a, x, y, st, budget, cfg, part);
@@ -563,39 +436,6 @@ hb_status pd_apply(hb_handle h, hb_dtype dt, const void *x, void *y, cudaStream_
 }
 
 int pd_hv_launches(hb_handle h, hb_dtype dt) { return !h->ks && h->hv_cfg[dt].split ? 2 : 1; }
-
-bool pd_fx_step_fuses(hb_handle h) {
-    if (h->ks || !h->fx_ok || !h->hv_cfg[HB_FX64].split || !h->dn.wb_ok || h->dn.wb_nblk == 0) return false;
-    int max_smem = 0;
-    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    FxArgs a;
-    a.Dd = h->D_dn;
-    a.wb_nblk = h->dn.wb_nblk;
-    return fx_wb_rows(a, h->hv_cfg[HB_FX64], (size_t)max_smem) > 0;
-}
-
-hb_status pd_fx_step_hv(hb_handle h, const int64_t *v, const int64_t *vprev, const double *beta_prev, int64_t *w,
-                        void *partials, int max_blocks, int *nb, cudaStream_t st) {
-    if (!pd_fx_step_fuses(h) || max_blocks < 1 || !nb) return HB_ERR_INVALID_STATE;
-    FxArgs a;
-    size_t budget = 0;
-    hb_status s = make_fx_args(h, a, &budget);
-    if (s != HB_OK) return s;
-    const HvConfig &cfg = h->hv_cfg[HB_FX64];
-    const int R = fx_wb_rows(a, cfg, budget);
-    if (R == 0) return HB_ERR_INVALID_STATE;
-    const int64_t *vp = beta_prev ? vprev : nullptr;
-    pdx::I128 *part = static_cast<pdx::I128 *>(partials);
-    switch (std::max(1, h->n_classes)) {
-        case 1: return fx_step_nc<1>(h, a, v, w, vp, beta_prev, part, max_blocks, nb, st, cfg, R);
-        case 2: return fx_step_nc<2>(h, a, v, w, vp, beta_prev, part, max_blocks, nb, st, cfg, R);
-        case 3: return fx_step_nc<3>(h, a, v, w, vp, beta_prev, part, max_blocks, nb, st, cfg, R);
-        default: return fx_step_nc<4>(h, a, v, w, vp, beta_prev, part, max_blocks, nb, st, cfg, R);
-    }
-}
 
 namespace {
 

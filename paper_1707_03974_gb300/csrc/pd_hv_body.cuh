@@ -511,7 +511,7 @@ __device__ __forceinline__ void up_segment_fx(const int64_t *__restrict__ x, con
 // Epi: optional hook for the final value y_row + up of each element (the batched
 // Lanczos step fuses its first vector pass there); with the default (void) the
 // sum is stored back to y.
-template <int RR, int NC, bool IDX32, int V, class Epi = void, bool ASSIGN = false>
+template <int RR, int NC, bool IDX32, int V, class Epi = void>
 __device__ __forceinline__ void hv_fx_up_item(const FxArgs &a, const int64_t *__restrict__ x,
                                               int64_t *__restrict__ y, uint64_t j, uint64_t g, int W, int S,
                                               unsigned char *smem, Epi *epi = nullptr) {
@@ -555,15 +555,9 @@ __device__ __forceinline__ void hv_fx_up_item(const FxArgs &a, const int64_t *__
             for (int v = 0; v < V; ++v) add[v] += (uint64_t)fx_mul(pos[v] - neg[v], a.Kc[cc], a.Gc[cc]);
         }
         Pack<int64_t, V> *yp = reinterpret_cast<Pack<int64_t, V> *>(y + u * Dd + d);
-        Pack<int64_t, V> yv;
-        if constexpr (ASSIGN) {  // y = spin-up term alone (the row pass adds the rest)
+        Pack<int64_t, V> yv = *yp;
 #pragma unroll
-            for (int v = 0; v < V; ++v) yv.v[v] = (int64_t)add[v];
-        } else {
-            yv = *yp;
-#pragma unroll
-            for (int v = 0; v < V; ++v) yv.v[v] = (int64_t)((uint64_t)yv.v[v] + add[v]);
-        }
+        for (int v = 0; v < V; ++v) yv.v[v] = (int64_t)((uint64_t)yv.v[v] + add[v]);
         if constexpr (std::is_void<Epi>::value) {
             *yp = yv;
         } else {
@@ -586,10 +580,9 @@ __host__ __device__ inline size_t hv_fx_wb_smem_bytes(int R, uint64_t Dd) {
     return off + (size_t)R * (Dd + 8) * 8;
 }
 
-template <int R, int NC, class Epi = void>
+template <int R, int NC>
 __device__ __forceinline__ void hv_fx_wb_group(const FxArgs &a, const int64_t *__restrict__ x,
-                                               int64_t *__restrict__ y, uint64_t g, unsigned char *smem,
-                                               Epi *epi = nullptr) {
+                                               int64_t *__restrict__ y, uint64_t g, unsigned char *smem) {
     const uint64_t Dd = a.Dd;
     const int64_t *s_kd = reinterpret_cast<const int64_t *>(smem);
     const int *s_gd = reinterpret_cast<const int *>(smem + 8 * (PD_MAXL + 1));
@@ -643,7 +636,6 @@ __device__ __forceinline__ void hv_fx_wb_group(const FxArgs &a, const int64_t *_
         const uint32_t col = a.wb_perm[p];
         if (col < Dd) {
             const uint32_t sd = a.wb_str[p];
-            if constexpr (!std::is_void<Epi>::value) epi->load(ur, nr, Dd, col);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (r >= nr) continue;
@@ -651,12 +643,8 @@ __device__ __forceinline__ void hv_fx_wb_group(const FxArgs &a, const int64_t *_
                 int64_t out = fx_mul(s_x[(uint64_t)col * R + r], s_kd[docc], s_gd[docc]);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) out += fx_mul(acc[r][2 * c] - acc[r][2 * c + 1], a.Kc[c], a.Gc[c]);
-                if constexpr (std::is_void<Epi>::value)
-                    y[ur[r] * Dd + col] = out;
-                else
-                    epi->put(r, ur[r] * Dd + col, out, s_x[(uint64_t)col * R + r]);
+                y[ur[r] * Dd + col] = out;
             }
         }
-        if constexpr (!std::is_void<Epi>::value) epi->block_done();
     }
 }

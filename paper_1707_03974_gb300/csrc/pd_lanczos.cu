@@ -632,22 +632,18 @@ hb_status three_term_step(Solve &s, hb_dtype dt, const T *v, const T *vp, T *w, 
     return HB_OK;
 }
 
-// The fixed-point step in two passes (see k_fx_axpy_dot3): 3 kernel launches
-// after the H·v.  Under the split H·v with the warp-blocked table the first pass
-// runs inside the H·v's row pass (pd_fx_step_hv: same w, same exact sums), and
-// the events ev0 / ev1 then bracket the H·v together with that pass.
+// The fixed-point step in two passes (see k_fx_axpy_dot3): 4 kernel launches
+// after the H·v.
 hb_status three_term_step_fx(Solve &s, const int64_t *v, const int64_t *vp, int64_t *w, const double *beta_prev,
                              double *alpha, double *beta, bool scale, cudaEvent_t ev0, cudaEvent_t ev1) {
-    int nb = s.nblk;
+    const int nb = s.nblk;
     I128 *part = reinterpret_cast<I128 *>(s.partials);
     const int F = s.h->fx_frac;
     if (ev0) PD_CUDA(cudaEventRecord(ev0, s.st));
-    const bool fused = pd_fx_step_fuses(s.h);
-    hb_status st = fused ? pd_fx_step_hv(s.h, v, vp, vp ? beta_prev : nullptr, w, part, s.nblk, &nb, s.st)
-                         : pd_apply(s.h, HB_FX64, v, w, s.st);
+    hb_status st = pd_apply(s.h, HB_FX64, v, w, s.st);
     if (st != HB_OK) return st;
     if (ev1) PD_CUDA(cudaEventRecord(ev1, s.st));
-    if (!fused) k_fx_axpy_dot3<<<nb, kRedThreads, 0, s.st>>>(w, vp, vp ? beta_prev : nullptr, v, s.D, part);
+    k_fx_axpy_dot3<<<nb, kRedThreads, 0, s.st>>>(w, vp, vp ? beta_prev : nullptr, v, s.D, part);
     k_fx_alpha_beta<<<1, kFinalThreads, 0, s.st>>>(part, nb, alpha, beta, F);
     k_fx_update<<<s.grid_vec, kRedThreads, 0, s.st>>>(w, v, alpha, beta, scale ? 1 : 0, s.D);
     PD_CUDA(cudaGetLastError());
@@ -916,19 +912,8 @@ hb_status lanczos_step(hb_handle h, hb_dtype dt, const void *v, const void *vpre
     else
         st = three_term_step<float>(s, dt, static_cast<const float *>(v), static_cast<const float *>(vprev),
                                     static_cast<float *>(w), beta_prev, alpha, beta, true, e0, e1);
-    if (st == HB_OK && launches)
-        *launches += (uint32_t)(pd_hv_launches(h, dt) + (dt == HB_F64 ? 5 : dt == HB_FX64 && pd_fx_step_fuses(h) ? 2 : 3));
+    if (st == HB_OK && launches) *launches += (uint32_t)(pd_hv_launches(h, dt) + (dt == HB_F64 ? 5 : 3));
     return st;
-}
-
-hb_status lanczos_step_fused(hb_handle h, hb_dtype dt, int *fused) {
-    if (!h || !fused || (dt != HB_F64 && dt != HB_F32 && dt != HB_FX64)) return HB_ERR_INVALID_ARG;
-    *fused = 0;
-    if (dt != HB_FX64 || !h->fx_ok) return HB_OK;
-    hb_status st = pd_build_tables(h);
-    if (st != HB_OK) return st;
-    *fused = pd_fx_step_fuses(h) ? 1 : 0;
-    return HB_OK;
 }
 
 hb_status lanczos_workspace_bytes(hb_handle h, const hb_lanczos_opts *o, uint64_t *bytes) {
@@ -1223,7 +1208,6 @@ extern "C" hb_status lanczos_step_noalloc(hb_handle h, hb_dtype dt, const void *
     else
         st = three_term_step<float>(s, dt, static_cast<const float *>(v), static_cast<const float *>(vprev),
                                     static_cast<float *>(w), beta_prev, alpha, beta, true, e0, e1);
-    if (st == HB_OK && launches)
-        *launches += (uint32_t)(pd_hv_launches(h, dt) + (dt == HB_F64 ? 5 : dt == HB_FX64 && pd_fx_step_fuses(h) ? 2 : 3));
+    if (st == HB_OK && launches) *launches += (uint32_t)(pd_hv_launches(h, dt) + (dt == HB_F64 ? 5 : 3));
     return st;
 }

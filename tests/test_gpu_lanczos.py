@@ -217,8 +217,7 @@ def test_fx64_step_tracks_f64_step(env):
 @pytest.mark.parametrize("dtype_name", ["float64", "int64", "float32"])
 def test_step_launch_count_and_unit_norm(env, dtype_name, split):
     """The launch counter matches the kernels enqueued (H·v 1 or 2, then 3 for the two-pass
-    fixed-point and float32 steps, 2 when the fixed-point step's first pass runs inside the
-    split H·v, or 5 for float64), and a step whose beta comes from the sums
+    fixed-point and float32 steps or 5 for float64), and a step whose beta comes from the sums
     <w,w> - 2 alpha <w,v> + alpha^2 <v,v> leaves a vector of unit norm."""
     import ctypes
     torch, pd = env
@@ -237,10 +236,7 @@ def test_step_launch_count_and_unit_norm(env, dtype_name, split):
     pd.lanczos_step(h, v, None, w, None, a[0:1], b[0:1], scratch, launches=n)
     pd.lanczos_step(h, w, v, w2, b[0:1], a[1:2], b[1:2], scratch, launches=n)
     torch.cuda.synchronize()
-    # the split fixed-point step runs its first vector pass inside the H·v row pass
-    fused = dtype_name == "int64" and split == 1
-    assert pd.lanczos_step_fused(h, dtype) == fused
-    per_step = (1 + split) + (5 if dtype_name == "float64" else 2 if fused else 3)
+    per_step = (1 + split) + (5 if dtype_name == "float64" else 3)
     assert n.value == 2 * per_step
     tol = 1e-6 if dtype_name == "float32" else 1e-14
     for vec in (w, w2):
