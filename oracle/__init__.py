@@ -24,7 +24,8 @@ Definitions used (each function cites the passage it follows):
   a textbook Lanczos run.
 
 Parity status: every function here is pinned by tests against values printed in
-the paper or fixed by mathematics (closed forms, invariants, brute force), except
-``count_below`` at L > 24, which is pinned only indirectly (it is the same
-counting definition checked against the sorted list for L <= 20).
+the paper or fixed by mathematics (closed forms, invariants, brute force).
+``count_below`` and ``string_at`` are checked against the sorted list for
+L <= 14 and, up to L = 32, along runs of the bit-operation successor of
+Sec. II A (which counts nothing): the count must grow by exactly one per step.
 """
