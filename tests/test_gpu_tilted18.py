@@ -65,6 +65,39 @@ def test_hv_tilted18_sampled_rows(env, dtype_name):
     torch.cuda.empty_cache()
 
 
+def test_hv_tilted18_fx64_split_long_rows(env):
+    """Fixed point in the split form, whose row pass gathers rows of 48,620 columns (389 KB,
+    longer than shared memory) from global memory: sampled rows against the counting oracle,
+    and the whole vector bit for bit against the one-kernel form."""
+    torch, pd, cl, h = env
+    m = Model.from_cluster(cl, U, 9, 9)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(81)
+    x = torch.empty(h.D, dtype=torch.float64, device="cuda")
+    x.uniform_(-1.0, 1.0, generator=g)
+    F = pd.hubbard_fixed_point_bits(h)
+    xin = pd.hubbard_convert(h, x, torch.int64)
+    del x
+    pd.hubbard_set_hv_config(h, torch.int64, 0, 0, 1)
+    ref = pd.hubbard_apply(h, xin)
+    pd.hubbard_set_hv_config(h, torch.int64, 0, 0, 1, split=1, up_block=256, up_threads=1024, up_rows=2)
+    y = pd.hubbard_apply(h, xin)
+    assert torch.equal(y, ref)
+    del ref
+    scale = 2.0 ** -F
+    rows = sampled_rows(h.D, 60, 5)
+    ys = y[torch.from_numpy(rows).cuda()].double().cpu().numpy() * scale
+    for r, yv in zip(rows, ys):
+        c, v = row_by_counting(m, int(r))
+        xc = xin[torch.from_numpy(c).cuda()].double().cpu().numpy() * scale
+        ref_r = float(np.dot(v, xc))
+        assert abs(yv - ref_r) <= 4 * scale + 64 * EPS64 * float(np.dot(np.abs(v), np.abs(xc))), (r, yv, ref_r)
+    pd.hubbard_set_hv_config(h, torch.int64, 0, 0, 1)
+    assert pd.hubbard_last_error(h) == "HB_OK"
+    del xin, y
+    torch.cuda.empty_cache()
+
+
 def test_tilted18_mixed_precision_matches_fixed_point_run(env):
     """float32 Krylov vectors + fixed-point finish vs an all-fixed-point run of the same cluster:
     E0 within 1e-10 (there is no CPU oracle at this size)."""
