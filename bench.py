@@ -560,10 +560,11 @@ def time_to_e0(pd, h, torch, tune=True):
     return res
 
 
-def precision_e0(pd, h, torch):
+def precision_e0(pd, h, torch, runs=("fx64", "plain_f64", "f32_only", "mixed_f32_fx64finish")):
     """18-site tilted cluster: E0 with float32 vectors (float64 scalars) and with the float32 phase plus a
     fixed-point finish, against the float64-grade fixed-point run of the same cluster and seed, and the
-    plain float64 solve for time.  Each vector type's H·v launch configuration is autotuned first."""
+    plain float64 solve for time.  Each vector type's H·v launch configuration is autotuned first.
+    `runs` picks a subset; errors are stated against the first run's E0."""
     for dt in (torch.int64, torch.float64):
         xa = torch.zeros(h.D, dtype=dt, device="cuda")
         ya = torch.empty_like(xa)
@@ -571,10 +572,12 @@ def precision_e0(pd, h, torch):
         del xa, ya
         torch.cuda.empty_cache()
     res = {}
-    for name, kw in (("fx64", dict(dtype=torch.int64, tol=1e-10)),
-                     ("plain_f64", dict(dtype=torch.float64, tol=1e-10)),
-                     ("f32_only", dict(dtype=torch.float32, tol=1e-6)),
-                     ("mixed_f32_fx64finish", dict(dtype=torch.float32, fp64_finish="fx64", tol=1e-10))):
+    kinds = {"fx64": dict(dtype=torch.int64, tol=1e-10),
+             "plain_f64": dict(dtype=torch.float64, tol=1e-10),
+             "f32_only": dict(dtype=torch.float32, tol=1e-6),
+             "mixed_f32_fx64finish": dict(dtype=torch.float32, fp64_finish="fx64", tol=1e-10)}
+    for name in runs:
+        kw = kinds[name]
         torch.cuda.empty_cache()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -582,9 +585,9 @@ def precision_e0(pd, h, torch):
         torch.cuda.synchronize()
         res[name] = {"seconds": round(time.perf_counter() - t0, 3), "iterations": r.iterations,
                      "iterations_f32": r.iterations_f32, "E0": r.E0, "residual": r.residual, "converged": r.converged}
-    ref = res["fx64"]["E0"]
+    ref = res[runs[0]]["E0"]
     for v in res.values():
-        v["abs_err_vs_fx64"] = abs(v["E0"] - ref)
+        v["abs_err_vs_" + runs[0]] = abs(v["E0"] - ref)
     return res
 
 
@@ -718,7 +721,7 @@ def measure_kspace(pd, torch, steps: int = 10):
                                 "converged": r.converged}}
 
 
-def measure_tilted18_f32(pd, torch, wl, steps: int = 5):
+def measure_tilted18_f32(pd, torch, wl, steps: int = 5, with_solve: bool = True):
     """The 18-site tilted cluster (U = 6, (9,9), D = 2,363,904,400) with float32 vectors and float64
     scalars: one Lanczos step and its H·v on the autotuned launch configuration."""
     cl = wl.tilted_18()
@@ -750,13 +753,20 @@ def measure_tilted18_f32(pd, torch, wl, steps: int = 5):
     step_ms = t0.elapsed_time(t1) / steps
     peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
     gbs = 8 * D / (hv_ms * 1e-3) / 1e9
-    del V
+    del V, scratch
+    torch.cuda.empty_cache()
+    # time to E0 at 1e-10 from the same seed: plain float64 against the float32 phase with a
+    # fixed-point finish (the precision claim of this configuration)
+    tte = precision_e0(pd, h, torch, runs=("plain_f64", "mixed_f32_fx64finish")) if with_solve else None
     h.close()
     torch.cuda.empty_cache()
-    return {"workload": "hubbard_18site_tilted_U6_half_filling", "D": D, "vector_dtype": "f32",
-            "step_ms": round(step_ms, 3), "hv_ms": round(hv_ms, 3), "value_gstates_per_s": round(D / (step_ms * 1e-3) / 1e9, 3),
-            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(gbs / peak, 4), "bytes_per_state": 8}}
+    out = {"workload": "hubbard_18site_tilted_U6_half_filling", "D": D, "vector_dtype": "f32",
+           "step_ms": round(step_ms, 3), "hv_ms": round(hv_ms, 3), "value_gstates_per_s": round(D / (step_ms * 1e-3) / 1e9, 3),
+           "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbs / peak, 4), "bytes_per_state": 8}}
+    if tte:
+        out["time_to_E0"] = tte
+    return out
 
 
 def measure_learned_quick(pd, torch, wl):
