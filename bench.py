@@ -395,6 +395,7 @@ def run_ours(args, world, rank, local):
         extra["kspace4x4_K00"] = measure_kspace(pd, torch)
         extra["tilted18_f32"] = measure_tilted18_f32(pd, torch, wl)
         extra["learned4x4"] = measure_learned_quick(pd, torch, wl)
+        extra["maps"] = measure_maps(pd, torch, wl)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -766,6 +767,54 @@ def measure_tilted18_f32(pd, torch, wl, steps: int = 5, with_solve: bool = True)
                         "frac": round(gbs / peak, 4), "bytes_per_state": 8}}
     if tte:
         out["time_to_E0"] = tte
+    return out
+
+
+def measure_maps(pd, torch, wl, reps: int = 5):
+    """Rank and unrank over whole bases (Eq. 3 and the backward map; Sec. IV B for the inversion-symmetric
+    maps): every index of the 4x4 half-filled basis (D = 165,636,900) unranked to its combined string and
+    ranked back, and every representative of the inversion-symmetric basis of 15 particles on 30 sites,
+    each timed with CUDA events (best of reps) after one warm-up; the round trips must give back every
+    index exactly.  Algorithmic traffic: 8 B read + 8 B written per element."""
+    peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+
+    def timed(fn):
+        fn()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return out, best
+
+    def record(n, ms):
+        return {"ms": round(ms, 4), "gelements_per_s": round(n / (ms * 1e-3) / 1e9, 3),
+                "hbm_frac": round(16 * n / (ms * 1e-3) / 1e9 / peak, 4)}
+
+    out = {}
+    cl = wl.square_periodic(4, 1.0, -0.3)
+    h = pd.Handle(cl.L, cl.bonds, cl.t, 8.0, 8, 8)
+    idx = torch.arange(h.D, dtype=torch.int64, device="cuda")
+    states, t_un = timed(lambda: pd.paradeisos_unrank(h, idx))
+    back, t_rk = timed(lambda: pd.paradeisos_rank(h, states))
+    out["combined_4x4_half"] = {"D": h.D, "unrank": record(h.D, t_un), "rank": record(h.D, t_rk),
+                                "round_trip_exact": bool(torch.equal(back, idx)),
+                                "status": pd.hubbard_last_error(h)}
+    del idx, states, back
+    h.close()
+    inv = pd.Inversion(30, 15)
+    idx = torch.arange(inv.D, dtype=torch.int64, device="cuda")
+    states, t_un = timed(lambda: inv.unrank(idx))
+    back, t_rk = timed(lambda: inv.rank(states))
+    out["inversion_30_15"] = {"D": inv.D, "unrank": record(inv.D, t_un), "rank": record(inv.D, t_rk),
+                              "round_trip_exact": bool(torch.equal(back, idx)), "status": inv.last_error()}
+    del idx, states, back
+    inv.close()
+    torch.cuda.empty_cache()
     return out
 
 
