@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "pd_common.cuh"
+#include "pd_divmagic.h"
 #include "pd_wb_sched.h"
 
 namespace {
@@ -63,7 +64,7 @@ __global__ void k_rank(const uint32_t *__restrict__ g_lut, const uint64_t *__res
 
 __global__ void k_unrank(const uint32_t *__restrict__ g_lut, const uint64_t *__restrict__ idx,
                          uint64_t *__restrict__ states, uint64_t n, int L, int N_up, int N_dn, uint64_t D_dn,
-                         uint64_t D, unsigned *err) {
+                         DivMagic by_dn, uint64_t D, unsigned *err) {
     __shared__ uint32_t lut[PD_LUT_W * PD_LUT_W];
     load_lut(lut, g_lut);
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
@@ -73,7 +74,7 @@ __global__ void k_unrank(const uint32_t *__restrict__ g_lut, const uint64_t *__r
             atomicOr(err, PD_ERRBIT(HB_ERR_OUT_OF_RANGE));
             continue;
         }
-        const uint64_t iu = I / D_dn;
+        const uint64_t iu = divmagic_q(I, by_dn);  // I / D_dn
         const uint64_t id = I - iu * D_dn;
         const uint64_t up = pd_backward_map(lut, (uint32_t)iu, N_up, L);
         const uint64_t dn = pd_backward_map(lut, (uint32_t)id, N_dn, L);
@@ -679,7 +680,8 @@ hb_status paradeisos_unrank(hb_handle h, const uint64_t *idx, uint64_t *states, 
     if (n == 0) return HB_OK;
     if (h->ks) return pd_k_unrank(h, idx, states, n, as_stream(stream));
     k_unrank<<<grid_for(n, h->sm_count), kThreads, 0, as_stream(stream)>>>(h->d_binom, idx, states, n, h->L,
-                                                                           h->N_up, h->N_dn, h->D_dn, h->D, h->d_err);
+                                                                           h->N_up, h->N_dn, h->D_dn,
+                                                                           make_divmagic(h->D_dn), h->D, h->d_err);
     PD_CUDA(cudaGetLastError());
     return HB_OK;
 }
